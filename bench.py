@@ -1,0 +1,364 @@
+"""Benchmark: cache records/s (L + grad + Hessian + radius) and queries/s on one GB300.
+
+A step is one pass of the whole hot path over one batch of the mid workload
+(2,048-triangle box field, sigma_t = 1, albedo 0.8, g = 0.5): 4,096 records with
+32 x 64 stratified rays each (compute_records), the record grid
+(build_record_grid) and 1,048,576 interpolation queries (query_inscatter).
+`value` is records per second of the whole step; queries per second of the same
+step, per-phase rates, the roofline of the record kernel, the end-to-end rate
+through host buffers and the FP64 oracle timed on the host cores are reported in
+the same JSON line.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own independent batch (weak scaling, no
+collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import platform
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "records/s (L_i+grad+Hessian) and queries/s at stated oracle error; learned vs plain"
+# FP32 operations of one lit cell in the record kernel (FMA = 2, division, square root,
+# exp and atan2 = 1), counted from cell_eval's source for the anisotropic path (g != 0):
+# solid angle and derivatives 318, phase function and derivatives 135, the accumulation
+# adds 30 and the Hessian norm 14, plus 213 per tied furthest vertex (transmittance,
+# product rule, RGB scatter).  See DESIGN.md, "Record kernel roofline".
+FLOP_CELL_BASE = 318 + 135 + 30 + 14
+FLOP_PER_FAR_VERTEX = 213
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except (OSError, ValueError):
+            pass
+    return None
+
+
+def fp32_peak_tflops(sm_mhz: float = 2070.0) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def flop_per_launch(n_cells: np.ndarray, n_far: np.ndarray) -> float:
+    return float(n_cells.astype(np.float64).sum()) * FLOP_CELL_BASE + float(n_far.astype(np.float64).sum()) * \
+        FLOP_PER_FAR_VERTEX
+
+
+# --------------------------------------------------------------------- oracle arm
+def oracle_rates(w, n_rec_sample: int, n_q_sample: int, threads: int):
+    """Time the FP64 oracle as it stands: records on `threads` host cores, brute-force
+    queries against the full record table on one core.  Returns per-unit rates."""
+    import oracle
+    pos = w.positions()
+    osc = oracle.OracleScene(w.scene)
+    idx = np.arange(n_rec_sample)
+    t0 = time.perf_counter()
+    r = oracle.records(osc, w.params, pos[idx], rec_ids=idx, n_threads=threads)
+    t_rec = time.perf_counter() - t0
+    rec_rate = n_rec_sample / t_rec
+    # a full-size record table for the query timing: the sampled records tiled with their
+    # own radii over all positions (the query cost depends on the table size and radii)
+    n = w.n_records
+    tab = {k: np.resize(r[k], (n,) + r[k].shape[1:]) for k in ("radius", "L", "grad", "hess")}
+    q = w.queries(n_q_sample)
+    t0 = time.perf_counter()
+    oracle.query(pos, tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=w.params.extrap_order)
+    t_q = time.perf_counter() - t0
+    return rec_rate, n_q_sample / t_q, t_rec + t_q
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    n_rec, n_q = 192, 16384
+    # warm-up steps (untimed) then K timed steps of the bounded sample
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_rates(w, 16, 1024, threads)
+    times = []
+    rr = qr = None
+    for _ in range(args.steps):
+        rr, qr, _ = oracle_rates(w, n_rec, n_q, threads)
+        times.append(w.n_records / rr + w.n_queries / qr)
+    t_step = float(np.mean(times))
+    value = w.n_records / t_step
+    sample = (f"{n_rec} records of the {w.n_records}-record batch on {threads} threads and {n_q} of the "
+              f"{w.n_queries} queries (brute force, 1 thread) per step; full-step time extrapolated per unit")
+    line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "records": w.n_records, "rays_per_record": w.params.n_rays,
+                       "queries": w.n_queries, "l2": "n/a (CPU)"},
+            "impl": "reference", "queries_per_s": w.n_queries / t_step,
+            "cpu_baseline": {"value": value, "unit": "records/s", "cores": threads, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model(), "records_per_s": rr, "queries_per_s": qr},
+            "e2e": {"value": value, "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gpu(args, w, rank, world, local_rank):
+    import torch
+    import paper_1805_09258_gb300 as vrc
+    from paper_1805_09258_gb300 import build as vbuild
+
+    if rank == 0:
+        vbuild.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        vbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rp = W.configs.with_params(w, rec_base=rank * w.n_records).params
+    pos_np = w.positions(seed=W.configs.SEED_RECORDS + 1000 * rank)
+    q_np = w.queries(seed=W.configs.SEED_QUERIES + 1000 * rank)
+    scene = vrc.Scene.from_workload(w.scene)
+    stream = torch.cuda.current_stream()
+    pos = torch.from_numpy(pos_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    rec = vrc.alloc_records(w.n_records, full=True, device=dev)
+    rgb = torch.empty((w.n_queries, 3), dtype=torch.float32, device=dev)
+    cnt = torch.empty((w.n_queries,), dtype=torch.int32, device=dev)
+    flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def step():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vrc.compute_records(scene, pos, rp, out=rec)
+        e1.record(stream)
+        grid = vrc.Grid(rec, extrap_order=rp.extrap_order)
+        e2.record(stream)
+        vrc.query_inscatter(grid, q, rgb, cnt)
+        e3.record(stream)
+        return (e0, e1, e2, e3), grid
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    keep = []
+    with ClockSampler(local_rank) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()                       # evict L2 between timed steps
+            ev, grid = step()
+            evs.append(ev)
+            keep.append(grid)
+        torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    t_rec = np.array([a.elapsed_time(b) for a, b, _, _ in evs])
+    t_grid = np.array([b.elapsed_time(c) for _, b, c, _ in evs])
+    t_q = np.array([c.elapsed_time(d) for _, _, c, d in evs])
+    t_step = t_rec + t_grid + t_q
+    ms = float(t_step.mean())
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms, float(t_rec.mean()), float(t_q.mean())], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, rec_ms, q_ms = [float(v) for v in tt.tolist()]
+    else:
+        rec_ms, q_ms = float(t_rec.mean()), float(t_q.mean())
+    value = world * w.n_records / (ms * 1e-3)
+    n_cells = rec["n_cells"].cpu().numpy()
+    n_far = rec["n_far"].cpu().numpy()
+    st = rec["status"].cpu().numpy()
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    h_pos = torch.from_numpy(pos_np).pin_memory()
+    h_q = torch.from_numpy(q_np).pin_memory()
+    h_rgb = torch.empty((w.n_queries, 3), dtype=torch.float32).pin_memory()
+    h_cnt = torch.empty((w.n_queries,), dtype=torch.int32).pin_memory()
+    h_out = {k: torch.empty(rec[k].shape, dtype=rec[k].dtype).pin_memory() for k in ("L", "grad", "hess", "radius")}
+    d_pos = torch.empty_like(pos)
+    d_q = torch.empty_like(q)
+
+    def e2e_step():
+        d_pos.copy_(h_pos, non_blocking=True)
+        d_q.copy_(h_q, non_blocking=True)
+        vrc.compute_records(scene, d_pos, rp, out=rec)
+        grid = vrc.Grid(rec, extrap_order=rp.extrap_order)
+        vrc.query_inscatter(grid, d_q, rgb, cnt)
+        for k, v in h_out.items():
+            v.copy_(rec[k], non_blocking=True)
+        h_rgb.copy_(rgb, non_blocking=True)
+        h_cnt.copy_(cnt, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return grid
+
+    for _ in range(2):
+        e2e_step()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t))
+    h2d = h_pos.numel() * 4 + h_q.numel() * 4
+    d2h = sum(v.numel() * 4 for v in h_out.values()) + h_rgb.numel() * 4 + h_cnt.numel() * 4
+
+    line = None
+    if rank == 0:
+        clk = clocks.summary()
+        peaks = measured_peaks()
+        fp32_peak = fp32_peak_tflops(2070.0)
+        flop = flop_per_launch(n_cells, n_far)
+        achieved = flop / (rec_ms * 1e-3) / 1e12
+        line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 (f64 eigen-solve)", "data": "synthetic",
+                "config": {"workload": w.name, "records": w.n_records, "rays_per_record": w.params.n_rays,
+                           "queries": w.n_queries, "scene_tris": w.scene.n_tris,
+                           "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                "queries_per_s": world * w.n_queries / (ms * 1e-3),
+                "phases_ms": {"compute_records": rec_ms, "build_record_grid": float(t_grid.mean()),
+                              "query_inscatter": q_ms},
+                "records_per_s_kernel": w.n_records / (rec_ms * 1e-3),
+                "queries_per_s_kernel": w.n_queries / (q_ms * 1e-3),
+                "roofline": {"kernel": "k_records", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                             "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                             "lit_cells_per_launch": int(n_cells.sum()), "far_vertex_evals": int(n_far.sum()),
+                             "flop_per_launch": flop},
+                "clocks": clk,
+                "e2e": {"value": world * w.n_records / e2e_s, "unit": "records/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
+                "gpu_launches": None,
+                "record_status": {"ok": int((st == 0).sum()), "clamped": int(((st & 6) != 0).sum()),
+                                  "nonfinite": int(((st & 1) != 0).sum())},
+                "peaks_file": bool(peaks)}
+        # kernels launched per step: 1 memset-free counter reset is a cudaMemset (not ours);
+        # records 1, grid: pack + count + 3 scan + fill + sort = 7, queries: 3 scan + bin +
+        # scatter + query = 6
+        line["gpu_launches"] = args.steps * (1 + 7 + 6)
+        if not args.no_cpu_baseline:
+            rr, qr, spent = oracle_rates(w, 96, 8192, os.cpu_count() or 1)
+            t_cpu = w.n_records / rr + w.n_queries / qr
+            line["cpu_baseline"] = {"value": w.n_records / t_cpu, "unit": "records/s", "cores": os.cpu_count(),
+                                    "kind": "oracle", "cpu": cpu_model(),
+                                    "sample": "96 of the 4,096 records (all host threads) and 8,192 of the 1M "
+                                              "queries (brute force, 1 thread); full-step time extrapolated",
+                                    "records_per_s": rr, "queries_per_s": qr, "seconds": spent}
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = W.config2()
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_gpu(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * vrc.h -- C ABI of the GB300 (sm_103a) library for second-order occlusion-aware
+ * volumetric radiance caching (Marco, Jarabo, Jarosz, Gutierrez, "Second-Order
+ * Occlusion-Aware Volumetric Radiance Caching", ACM TOG 37(2), 2018).
+ *
+ * The library computes cache records -- in-scattered radiance L together with its
+ * occlusion-aware translational gradient and Hessian at a point x of a homogeneous
+ * medium -- and answers interpolation queries from them.  Every step runs in the
+ * library's own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ *   - The participating medium fills the unit cube [0,1]^3; all geometry lies in it.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; other pointers
+ *     are host pointers, read during the call only.  Opaque objects (vrc_scene,
+ *     vrc_grid, vrc_mlp) are owned by the library and freed by their destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (0 = the legacy default stream).
+ *     Calls that take a stream are asynchronous on it unless documented otherwise.
+ *   - Every call returns an int status: VRC_OK (0) or a negative VRC_ERR_* code;
+ *     vrc_status_string() names it.  No C++ exception crosses the ABI.  Per-item
+ *     outcomes (a record whose radius was clamped, a query that found no record)
+ *     go to caller-provided status arrays.
+ *   - Vectors are float32 xyz; RGB triples are float32 r,g,b.  A gradient of an
+ *     RGB quantity is stored [channel][axis] (9 floats), a Hessian [channel][6]
+ *     with the 6 unique entries in the order xx, xy, xz, yy, yz, zz (18 floats).
+ */
+#ifndef VRC_H
+#define VRC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define VRC_OK 0
+#define VRC_ERR_INVALID -1      /* a null pointer, size or parameter out of range */
+#define VRC_ERR_OOM -2          /* a device or host allocation failed */
+#define VRC_ERR_CUDA -3         /* a CUDA runtime call failed (launch, copy) */
+#define VRC_ERR_TIMEOUT -4      /* a bounded device-side wait gave up */
+#define VRC_ERR_UNSUPPORTED -5  /* a size beyond what the kernels handle */
+
+/* per-record status bits (vrc_records_view.status) */
+#define VRC_REC_NONFINITE 1     /* a non-finite value was produced */
+#define VRC_REC_CLAMP_LO 2      /* radius clamped to r_min (or L <= 0) */
+#define VRC_REC_CLAMP_HI 4      /* radius clamped to r_max (or a zero Hessian) */
+#define VRC_REC_DEGENERATE 8    /* at least one cell had A = B = 0 and was skipped */
+
+/* --------------------------------------------------------------- scene */
+/* Homogeneous medium (Sec. 3, Table 1): scattering and absorption coefficients and
+ * the Henyey-Greenstein asymmetry g of the phase function. */
+typedef struct { float sigma_s, sigma_a, g; } vrc_medium;
+
+/* Point light (handled by shadow rays, Sec. 6 "Implementation"). */
+typedef struct { float pos[3]; float intensity[3]; } vrc_point_light;
+
+#define VRC_MAX_LIGHTS 4
+
+typedef struct vrc_scene vrc_scene;
+
+/* Build a scene: uploads the triangles, builds a bounding volume hierarchy on the
+ * host and keeps it on the device.  verts_xyz [n_verts][3], tri_idx [n_tris][3]
+ * (indices into verts), albedo_rgb [n_tris][3] (Lambertian, two-sided),
+ * emission_rgb [n_tris][3] or NULL, lights [n_lights] with n_lights <= VRC_MAX_LIGHTS.
+ * Synchronous.  Returns VRC_ERR_INVALID for bad sizes or indices, VRC_ERR_OOM. */
+int vrc_build_scene(const float* verts_xyz, int32_t n_verts, const int32_t* tri_idx, int32_t n_tris,
+                    const float* albedo_rgb, const float* emission_rgb, const vrc_medium* medium,
+                    const vrc_point_light* lights, int32_t n_lights, vrc_scene** out);
+void vrc_destroy_scene(vrc_scene* scene);
+
+/* --------------------------------------------------------------- records */
+/* Per-call record parameters.
+ *   n_bands x n_bins  stratified ray set: equal d(cos theta) x equal d(phi) strata,
+ *                     one jittered ray each, plus two unweighted pole rays
+ *                     (Sec. 6 "Implementation": equal solid angle strata)
+ *   dt                march step of the distance shells (Sec. 6)
+ *   eps               error tolerance of the radius (Eq. radiusAniso3D)
+ *   omega_o           outgoing direction of the phase function (unit vector)
+ *   seed              jitter seed (splitmix64 counter generator)
+ *   ff_signed         1: signed solid angle (closes every shell); 0: |A| as printed in App. C
+ *   extrap_order      1 (Eq. radianceTaylor) or 2 (adds the Hessian term); used by the grid
+ *   r_min, r_max      radius clamps
+ *   rec_base          jitter index of record 0 (record i uses rec_base + i) */
+typedef struct {
+    int32_t n_bands, n_bins;
+    float dt, eps;
+    float omega_o[3];
+    uint64_t seed;
+    int32_t ff_signed;
+    int32_t extrap_order;
+    float r_min, r_max;
+    int64_t rec_base;
+} vrc_record_params;
+
+/* Caller-allocated device outputs of vrc_compute_records, one row per record.
+ * Required: L, grad, hess, radius, status, pos.  Others may be NULL.
+ *   L [n][3]        Monte Carlo in-scattered radiance (Eq. outLF, Sec. 4 last paragraph)
+ *   grad [n][9]     occlusion-aware gradient (Eq. SegmentRadianceGradient)
+ *   hess [n][18]    occlusion-aware Hessian (Eq. SegmentRadianceHessian)
+ *   *_ss / *_ms     the same split into surface-shell (single scattering, surface
+ *                   radiance) and medium-shell (second bounce) parts
+ *   L_ff [n][3]     triangulated radiance of Eq. ApprxRadiance (diagnostic)
+ *   radius [n]      validity radius (Eq. radiusAniso3D with the largest |eigenvalue|)
+ *   eig [n][3]      eigenvalues of the luminance Hessian, ascending
+ *   kappa [n]       sum of per-cell Hessian norms / norm of their sum (conditioning)
+ *   status [n]      VRC_REC_* bits
+ *   pos [n][3]      the record centres (copied from d_pos)
+ *   n_cells [n]     cells evaluated (lit cells of all shells; work counter), NULL to skip
+ *   n_far [n]       furthest-vertex evaluations (sum of tie sizes over lit cells), NULL to skip
+ *   n_shells [n]    medium shells K = ceil(max t_end / dt), NULL to skip
+ *   hit_prim, hit_t [n][dbg_stride]  per-ray primary hit id (-1 = escaped) and t,
+ *                   for rays v < n_bands*n_bins + 2; NULL to skip */
+typedef struct {
+    float* L;
+    float* grad;
+    float* hess;
+    float* L_ss;
+    float* grad_ss;
+    float* hess_ss;
+    float* L_ms;
+    float* grad_ms;
+    float* hess_ms;
+    float* L_ff;
+    float* radius;
+    float* eig;
+    float* kappa;
+    int32_t* status;
+    float* pos;
+    int32_t* n_cells;
+    int32_t* n_far;
+    int32_t* n_shells;
+    int32_t* hit_prim;
+    float* hit_t;
+    int32_t dbg_stride;
+} vrc_records_view;
+
+/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default. */
+typedef struct {
+    int32_t threads;        /* threads per block: 128, 256, 512 */
+    int32_t chunk_bands;    /* bands of the ray set kept in shared memory at once */
+    int32_t blocks_per_sm;  /* persistent blocks per SM */
+} vrc_record_tuning;
+
+/* Compute n records at d_pos [n][3] (Secs. 4-5 and App. A, C): trace the stratified
+ * ray set through the scene, build the distance shells (zero-radiance samples at
+ * occluders), evaluate every cell's form factor, transmittance and phase terms with
+ * their derivatives, reduce them into L, grad L and H L, and set each radius from the
+ * Hessian's eigenvalues.  d_n_bands [n] (nullable) gives per-record band counts with
+ * bins = 2 * bands (mixed ray counts in one persistent launch).  Asynchronous on
+ * `stream`.  VRC_ERR_INVALID for null required outputs, n < 0, bands < 1, bins < 3;
+ * VRC_ERR_UNSUPPORTED for more than 256 bands or 512 bins. */
+int vrc_compute_records(vrc_scene* scene, const float* d_pos, int32_t n, const int32_t* d_n_bands,
+                        const vrc_record_params* params, const vrc_records_view* d_out, void* stream);
+
+/* Same computation from HOST buffers: h_pos [n][3] in, h_L [n][3], h_grad [n][9],
+ * h_hess [n][18], h_radius [n], h_status [n] out (any output may be NULL).  Copies
+ * in and out through device buffers owned by the scene; synchronous. */
+int vrc_compute_records_host(vrc_scene* scene, const float* h_pos, int32_t n, const vrc_record_params* params,
+                             float* h_L, float* h_grad, float* h_hess, float* h_radius, int32_t* h_status);
+
+int vrc_set_record_tuning(vrc_scene* scene, const vrc_record_tuning* tuning);
+int vrc_get_record_tuning(const vrc_scene* scene, vrc_record_tuning* tuning);
+
+/* --------------------------------------------------------------- queries */
+typedef struct vrc_grid vrc_grid;
+
+/* Build the lookup structure for Eq. radianceTaylor from n device records (pos,
+ * radius, L, grad and, for extrap_order 2, hess of `recs`): a compact record table
+ * and a uniform grid over the unit cube whose cells list every record whose sphere
+ * of radius R_k overlaps them.  The grid owns copies; `recs` may be freed after the
+ * call completes on `stream`.  Synchronous (reads back the list size). */
+int vrc_build_record_grid(const vrc_records_view* recs, int32_t n, int32_t extrap_order, vrc_grid** out,
+                          void* stream);
+void vrc_destroy_grid(vrc_grid* grid);
+
+/* Answer nq queries d_q [nq][3] by Eq. radianceTaylor: the weighted first-order (or,
+ * with extrap_order 2, second-order) Taylor extrapolation from every record k with
+ * |x' - x_k| < R_k, weight w = 3d^2 - 2d^3, d = 1 - |x' - x_k| / R_k.  Writes d_rgb
+ * [nq][3] and d_status [nq] = number of contributing records (0 = miss, rgb = 0).
+ * Asynchronous on `stream`. */
+int vrc_query_inscatter(const vrc_grid* grid, const float* d_q, int32_t nq, float* d_rgb, int32_t* d_status,
+                        void* stream);
+
+/* --------------------------------------------------------------- misc */
+const char* vrc_status_string(int status);
+int vrc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VRC_H */

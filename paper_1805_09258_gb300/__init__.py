@@ -1,0 +1,277 @@
+"""Python binding of libvrc (second-order occlusion-aware volumetric radiance caching).
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+(libvrc.so, built from csrc/ for sm_103a).  PyTorch supplies device memory and the
+current stream.  There is no CPU fallback: if the library cannot be loaded or no
+CUDA device is present, every call raises.
+
+Names follow the C ABI in include/vrc.h: build_scene, compute_records,
+compute_records_host, build_record_grid, query_inscatter.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvrc.so")
+
+VRC_OK, VRC_ERR_INVALID, VRC_ERR_OOM, VRC_ERR_CUDA, VRC_ERR_TIMEOUT, VRC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+REC_NONFINITE, REC_CLAMP_LO, REC_CLAMP_HI, REC_DEGENERATE = 1, 2, 4, 8
+MAX_LIGHTS = 4
+
+
+class VrcError(RuntimeError):
+    pass
+
+
+class _Medium(C.Structure):
+    _fields_ = [("sigma_s", C.c_float), ("sigma_a", C.c_float), ("g", C.c_float)]
+
+
+class _Light(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+class RecordParamsC(C.Structure):
+    _fields_ = [("n_bands", C.c_int32), ("n_bins", C.c_int32), ("dt", C.c_float), ("eps", C.c_float),
+                ("omega_o", C.c_float * 3), ("seed", C.c_uint64), ("ff_signed", C.c_int32),
+                ("extrap_order", C.c_int32), ("r_min", C.c_float), ("r_max", C.c_float), ("rec_base", C.c_int64)]
+
+
+class RecordsView(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms",
+                                           "hess_ms", "L_ff", "radius", "eig", "kappa", "status", "pos",
+                                           "n_cells", "n_far", "n_shells", "hit_prim", "hit_t")] + [("dbg_stride", C.c_int32)]
+
+
+class RecordTuning(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("chunk_bands", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libvrc.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise VrcError(f"libvrc.so not built ({p}); run paper_1805_09258_gb300.build.build()")
+    L = C.CDLL(p)
+    P, I32 = C.c_void_p, C.c_int32
+    L.vrc_build_scene.argtypes = [P, I32, P, I32, P, P, P, P, I32, C.POINTER(C.c_void_p)]
+    L.vrc_destroy_scene.argtypes = [P]
+    L.vrc_destroy_scene.restype = None
+    L.vrc_compute_records.argtypes = [P, P, I32, P, P, P, P]
+    L.vrc_compute_records_host.argtypes = [P, P, I32, P, P, P, P, P, P]
+    L.vrc_set_record_tuning.argtypes = [P, P]
+    L.vrc_get_record_tuning.argtypes = [P, P]
+    L.vrc_build_record_grid.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
+    L.vrc_destroy_grid.argtypes = [P]
+    L.vrc_destroy_grid.restype = None
+    L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
+    L.vrc_status_string.restype = C.c_char_p
+    L.vrc_status_string.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != VRC_OK:
+        msg = load_library().vrc_status_string(rc).decode()
+        raise VrcError(f"{what} failed: {msg} ({rc})")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise VrcError("no CUDA device: libvrc runs on the GPU only")
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def record_params(rp) -> RecordParamsC:
+    """Marshal any object with the RecordParams fields into the C struct."""
+    p = RecordParamsC()
+    p.n_bands, p.n_bins = int(rp.n_bands), int(rp.n_bins)
+    p.dt, p.eps = float(rp.dt), float(rp.eps)
+    p.omega_o[:] = [float(v) for v in rp.omega_o]
+    p.seed = int(rp.seed)
+    p.ff_signed, p.extrap_order = int(rp.ff_signed), int(rp.extrap_order)
+    p.r_min, p.r_max = float(rp.r_min), float(rp.r_max)
+    p.rec_base = int(getattr(rp, "rec_base", 0))
+    return p
+
+
+class Scene:
+    """A scene on the device (vrc_build_scene / vrc_destroy_scene)."""
+
+    def __init__(self, tris, albedo, medium, lights, emission=None):
+        L = load_library()
+        tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 3, 3)
+        n = tris.shape[0]
+        verts = np.ascontiguousarray(tris.reshape(-1, 3))
+        idx = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+        albedo = np.ascontiguousarray(albedo, dtype=np.float32).reshape(n, 3)
+        em = None if emission is None else np.ascontiguousarray(emission, dtype=np.float32).reshape(n, 3)
+        med = _Medium(float(medium.sigma_s), float(medium.sigma_a), float(medium.g))
+        nl = len(lights)
+        larr = (_Light * max(nl, 1))()
+        for i, l in enumerate(lights):
+            larr[i].pos[:] = [float(v) for v in l.pos]
+            larr[i].intensity[:] = [float(v) for v in l.intensity]
+        h = C.c_void_p()
+        rc = L.vrc_build_scene(verts.ctypes.data, verts.shape[0], idx.ctypes.data, n, albedo.ctypes.data,
+                               None if em is None else em.ctypes.data, C.byref(med), C.byref(larr), nl, C.byref(h))
+        _check(rc, "vrc_build_scene")
+        self.handle = h
+        self.n_tris = n
+
+    @classmethod
+    def from_workload(cls, scene):
+        return cls(scene.tris, scene.albedo, scene.medium, scene.lights, scene.emission)
+
+    def set_tuning(self, threads=0, chunk_bands=0, blocks_per_sm=0):
+        t = RecordTuning(threads, chunk_bands, blocks_per_sm)
+        _check(load_library().vrc_set_record_tuning(self.handle, C.byref(t)), "vrc_set_record_tuning")
+
+    def get_tuning(self):
+        t = RecordTuning()
+        _check(load_library().vrc_get_record_tuning(self.handle, C.byref(t)), "vrc_get_record_tuning")
+        return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) and _lib is not None:
+                _lib.vrc_destroy_scene(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+build_scene = Scene
+
+RECORD_FIELDS = dict(L=3, grad=9, hess=18, L_ss=3, grad_ss=9, hess_ss=18, L_ms=3, grad_ms=9, hess_ms=18,
+                     L_ff=3, radius=1, eig=3, kappa=1, pos=3)
+
+
+def alloc_records(n: int, full: bool = True, device="cuda"):
+    """Allocate the per-record output tensors (float32; status int32)."""
+    torch = _torch()
+    out = {}
+    for k, w in RECORD_FIELDS.items():
+        if not full and k not in ("L", "grad", "hess", "radius", "pos"):
+            continue
+        out[k] = torch.empty((n, w) if w > 1 else (n,), dtype=torch.float32, device=device)
+    out["status"] = torch.empty((n,), dtype=torch.int32, device=device)
+    if full:
+        out["n_cells"] = torch.empty((n,), dtype=torch.int32, device=device)
+        out["n_far"] = torch.empty((n,), dtype=torch.int32, device=device)
+        out["n_shells"] = torch.empty((n,), dtype=torch.int32, device=device)
+    return out
+
+
+def records_view(out: dict, dbg_stride: int = 0) -> RecordsView:
+    v = RecordsView()
+    for k in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms", "hess_ms", "L_ff", "radius",
+              "eig", "kappa", "status", "pos", "n_cells", "n_far", "n_shells", "hit_prim", "hit_t"):
+        setattr(v, k, _ptr(out.get(k)))
+    v.dbg_stride = dbg_stride
+    return v
+
+
+def compute_records(scene: Scene, pos, params, n_bands=None, out: Optional[dict] = None, full: bool = True,
+                    debug_hits: bool = False, stream=None) -> dict:
+    """vrc_compute_records on device positions `pos` [n,3] (float32 CUDA tensor)."""
+    torch = _torch()
+    assert pos.is_cuda and pos.dtype == torch.float32 and pos.is_contiguous()
+    n = pos.shape[0]
+    if out is None:
+        out = alloc_records(n, full=full, device=pos.device)
+    stride = 0
+    if debug_hits:
+        nb = int(params.n_bands)
+        ns = 2 * nb if n_bands is not None else int(params.n_bins)
+        stride = nb * ns + 2
+        out["hit_prim"] = torch.full((n, stride), -2, dtype=torch.int32, device=pos.device)
+        out["hit_t"] = torch.zeros((n, stride), dtype=torch.float32, device=pos.device)
+    v = records_view(out, stride)
+    p = record_params(params)
+    nbp = None
+    if n_bands is not None:
+        assert n_bands.is_cuda and n_bands.dtype == torch.int32
+        nbp = _ptr(n_bands)
+    rc = load_library().vrc_compute_records(scene.handle, _ptr(pos), n, nbp, C.byref(p), C.byref(v),
+                                            _stream_ptr(stream))
+    _check(rc, "vrc_compute_records")
+    return out
+
+
+def compute_records_host(scene: Scene, pos: np.ndarray, params) -> dict:
+    """vrc_compute_records_host: host positions in, host arrays out (synchronous)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)
+    n = pos.shape[0]
+    res = dict(L=np.zeros((n, 3), np.float32), grad=np.zeros((n, 9), np.float32),
+               hess=np.zeros((n, 18), np.float32), radius=np.zeros(n, np.float32), status=np.zeros(n, np.int32))
+    p = record_params(params)
+    rc = load_library().vrc_compute_records_host(scene.handle, pos.ctypes.data, n, C.byref(p),
+                                                 res["L"].ctypes.data, res["grad"].ctypes.data,
+                                                 res["hess"].ctypes.data, res["radius"].ctypes.data,
+                                                 res["status"].ctypes.data)
+    _check(rc, "vrc_compute_records_host")
+    return res
+
+
+class Grid:
+    """Record lookup structure (vrc_build_record_grid / vrc_destroy_grid)."""
+
+    def __init__(self, records: dict, n: Optional[int] = None, extrap_order: int = 1, stream=None):
+        n = records["L"].shape[0] if n is None else n
+        v = records_view(records)
+        h = C.c_void_p()
+        self._keep = records
+        rc = load_library().vrc_build_record_grid(C.byref(v), n, extrap_order, C.byref(h), _stream_ptr(stream))
+        _check(rc, "vrc_build_record_grid")
+        self.handle = h
+        self.n = n
+        self.extrap_order = extrap_order
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) and _lib is not None:
+                _lib.vrc_destroy_grid(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+build_record_grid = Grid
+
+
+def query_inscatter(grid: Grid, q, rgb=None, status=None, stream=None):
+    """vrc_query_inscatter on device query points q [nq,3]; returns (rgb [nq,3], count [nq])."""
+    torch = _torch()
+    assert q.is_cuda and q.dtype == torch.float32 and q.is_contiguous()
+    nq = q.shape[0]
+    if rgb is None:
+        rgb = torch.empty((nq, 3), dtype=torch.float32, device=q.device)
+    if status is None:
+        status = torch.empty((nq,), dtype=torch.int32, device=q.device)
+    rc = load_library().vrc_query_inscatter(grid.handle, _ptr(q), nq, _ptr(rgb), _ptr(status), _stream_ptr(stream))
+    _check(rc, "vrc_query_inscatter")
+    return rgb, status

@@ -1,0 +1,344 @@
+// query.cu -- radiance interpolation from cache records (Eq. radianceTaylor, Sec. 5).
+//
+// L(x') = sum_{k in C} w_k [L_k + grad L_k . (x' - x_k) (+ 1/2 D^T H_k D)] / sum_k w_k,
+// C = {k : |x' - x_k| < R_k}, w = 3 d^2 - 2 d^3, d = 1 - |x' - x_k| / R_k.
+//
+// The paper looks records up in an octree (Sec. 6); here the lookup is a uniform grid
+// over the unit cube whose cells list (CSR) every record whose sphere overlaps the
+// cell, so a query reads exactly one list.  Queries are first binned by cell (count,
+// scan, scatter) so the threads of a warp share one list: its record rows are read as
+// warp-wide broadcasts from L1.  Every buffer is owned by the vrc_grid object.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "vrc_internal.cuh"
+
+struct vrc_grid {
+    int n;                 // records
+    int G;                 // cells per axis
+    int order;             // 1 or 2
+    float4* rec;           // [n][4]: (pos, R), (L, g_r.x), (g_r.y, g_r.z, g_g.x, g_g.y), (g_g.z, g_b)
+    float4* hess;          // [n][5]: 18 Hessian entries (order 2), padded
+    int* cell_start;       // [G^3 + 1]
+    int* cell_list;        // [entries]
+    long long entries;
+    // query scratch (grown on demand)
+    int* q_cell;           // [cap]
+    int* q_rank;           // [cap]
+    int* q_perm;           // [cap]
+    int* q_count;          // [G^3 + 1]
+    int* scan_tmp;         // block sums
+    int q_cap;
+};
+
+namespace {
+
+constexpr int SCAN_BLOCK = 1024;
+
+__global__ void k_pack(const vrc_records_view v, int n, int order, float4* rec, float4* hess) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float* p = v.pos + 3 * k;
+    const float* L = v.L + 3 * k;
+    const float* g = v.grad + 9 * k;
+    rec[4 * k] = make_float4(p[0], p[1], p[2], v.radius[k]);
+    rec[4 * k + 1] = make_float4(L[0], L[1], L[2], g[0]);
+    rec[4 * k + 2] = make_float4(g[1], g[2], g[3], g[4]);
+    rec[4 * k + 3] = make_float4(g[5], g[6], g[7], g[8]);
+    if (order == 2) {
+        const float* h = v.hess + 18 * k;
+        for (int e = 0; e < 5; ++e)
+            hess[5 * k + e] = make_float4(h[4 * e], h[4 * e + 1], 4 * e + 2 < 18 ? h[4 * e + 2] : 0.f,
+                                          4 * e + 3 < 18 ? h[4 * e + 3] : 0.f);
+    }
+}
+
+__device__ __forceinline__ bool sphere_meets_cell(float3 c, float R, int ix, int iy, int iz, float h) {
+    float lx = ix * h, ly = iy * h, lz = iz * h;
+    float dx = fmaxf(fmaxf(lx - c.x, c.x - (lx + h)), 0.f);
+    float dy = fmaxf(fmaxf(ly - c.y, c.y - (ly + h)), 0.f);
+    float dz = fmaxf(fmaxf(lz - c.z, c.z - (lz + h)), 0.f);
+    return dx * dx + dy * dy + dz * dz < R * R;
+}
+
+// PASS 0: count (fill = false) or fill (fill = true) the cells each record's sphere overlaps
+template <bool FILL>
+__global__ void k_insert(const float4* rec, int n, int G, int* counts, const int* start, int* list) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float4 a = rec[4 * k];
+    float3 c = make_float3(a.x, a.y, a.z);
+    float R = a.w;
+    float h = 1.0f / G;
+    int x0 = max(0, (int)floorf((c.x - R) * G)), x1 = min(G - 1, (int)floorf((c.x + R) * G));
+    int y0 = max(0, (int)floorf((c.y - R) * G)), y1 = min(G - 1, (int)floorf((c.y + R) * G));
+    int z0 = max(0, (int)floorf((c.z - R) * G)), z1 = min(G - 1, (int)floorf((c.z + R) * G));
+    for (int ix = x0; ix <= x1; ++ix)
+        for (int iy = y0; iy <= y1; ++iy)
+            for (int iz = z0; iz <= z1; ++iz) {
+                if (!sphere_meets_cell(c, R, ix, iy, iz, h)) continue;
+                int cell = (ix * G + iy) * G + iz;
+                int slot = atomicAdd(&counts[cell], 1);
+                if (FILL) list[start[cell] + slot] = k;
+            }
+}
+
+// sort each cell's list ascending (deterministic summation order in the queries)
+__global__ void k_sort_lists(const int* start, int ncell, int* list) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ncell) return;
+    int b = start[cell], e = start[cell + 1];
+    for (int i = b + 1; i < e; ++i) {
+        int v = list[i], j = i - 1;
+        while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
+        list[j + 1] = v;
+    }
+}
+
+// exclusive scan of in[0, m) into out[0, m]; out[m] = total.  Two-level, block sums in tmp.
+__global__ void k_scan_blocks(const int* in, int m, int* out, int* tmp) {
+    __shared__ int s[SCAN_BLOCK];
+    int i = blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    int v = i < m ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+        int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < m) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == SCAN_BLOCK - 1) tmp[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_scan_tops(int* tmp, int nblk) {
+    // one thread: block counts are few (<= a few hundred)
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < nblk; ++b) {
+            int t = tmp[b];
+            tmp[b] = run;
+            run += t;
+        }
+        tmp[nblk] = run;
+    }
+}
+
+__global__ void k_scan_add(int* out, int m, const int* tmp, int nblk) {
+    int i = blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    if (i < m) out[i] += tmp[blockIdx.x];
+    if (i == 0) out[m] = tmp[nblk];
+}
+
+int exclusive_scan(const int* in, int m, int* out, int* tmp, cudaStream_t st) {
+    int nblk = (m + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    k_scan_blocks<<<nblk, SCAN_BLOCK, 0, st>>>(in, m, out, tmp);
+    k_scan_tops<<<1, 32, 0, st>>>(tmp, nblk);
+    k_scan_add<<<nblk, SCAN_BLOCK, 0, st>>>(out, m, tmp, nblk);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+__device__ __forceinline__ int cell_of(float3 q, int G) {
+    int ix = min(G - 1, max(0, (int)floorf(q.x * G)));
+    int iy = min(G - 1, max(0, (int)floorf(q.y * G)));
+    int iz = min(G - 1, max(0, (int)floorf(q.z * G)));
+    return (ix * G + iy) * G + iz;
+}
+
+__global__ void k_bin_queries(const float* q, int nq, int G, int* qcell, int* qrank, int* counts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    int c = cell_of(make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]), G);
+    qcell[i] = c;
+    qrank[i] = atomicAdd(&counts[c], 1);
+}
+
+__global__ void k_scatter_queries(const int* qcell, const int* qrank, const int* start, int nq, int* perm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    perm[start[qcell[i]] + qrank[i]] = i;
+}
+
+// one thread per query, in cell order
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, const float4* __restrict__ hess,
+                                               const int* __restrict__ cell_start, const int* __restrict__ list,
+                                               int G, const float* __restrict__ q, const int* __restrict__ perm,
+                                               int nq, float* __restrict__ rgb, int* __restrict__ status) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nq) return;
+    int i = perm[s];
+    float3 x = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+    int c = cell_of(x, G);
+    int b = cell_start[c], e = cell_start[c + 1];
+    float ar = 0.f, ag = 0.f, ab = 0.f, sw = 0.f;
+    int cnt = 0;
+    for (int p = b; p < e; ++p) {
+        int k = __ldg(&list[p]);
+        float4 a = __ldg(&rec[4 * k]);
+        float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
+        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(d2 < a.w * a.w)) continue;
+        float4 r1 = __ldg(&rec[4 * k + 1]), r2 = __ldg(&rec[4 * k + 2]), r3 = __ldg(&rec[4 * k + 3]);
+        float dd = 1.0f - sqrtf(d2) / a.w;
+        float w = dd * dd * fmaf(-2.0f, dd, 3.0f);
+        float vr = r1.x + fmaf(r1.w, dx, fmaf(r2.x, dy, r2.y * dz));
+        float vg = r1.y + fmaf(r2.z, dx, fmaf(r2.w, dy, r3.x * dz));
+        float vb = r1.z + fmaf(r3.y, dx, fmaf(r3.z, dy, r3.w * dz));
+        if (ORDER == 2) {
+            float4 h0 = __ldg(&hess[5 * k]), h1 = __ldg(&hess[5 * k + 1]), h2 = __ldg(&hess[5 * k + 2]),
+                   h3 = __ldg(&hess[5 * k + 3]), h4 = __ldg(&hess[5 * k + 4]);
+            float hh[18] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w, h2.x,
+                            h2.y, h2.z, h2.w, h3.x, h3.y, h3.z, h3.w, h4.x, h4.y};
+            float qv[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float* H = hh + 6 * ch;
+                qv[ch] = 0.5f * (H[0] * dx * dx + H[3] * dy * dy + H[5] * dz * dz) +
+                         (H[1] * dx * dy + H[2] * dx * dz + H[4] * dy * dz);
+            }
+            vr += qv[0];
+            vg += qv[1];
+            vb += qv[2];
+        }
+        ar = fmaf(w, vr, ar);
+        ag = fmaf(w, vg, ag);
+        ab = fmaf(w, vb, ab);
+        sw += w;
+        ++cnt;
+    }
+    float inv = cnt ? 1.0f / sw : 0.0f;
+    rgb[3 * i] = ar * inv;
+    rgb[3 * i + 1] = ag * inv;
+    rgb[3 * i + 2] = ab * inv;
+    status[i] = cnt;
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t count) {
+    if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        *p = nullptr;
+        return VRC_ERR_OOM;
+    }
+    return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" void vrc_destroy_grid(vrc_grid* g) {
+    if (!g) return;
+    cudaFree(g->rec);
+    cudaFree(g->hess);
+    cudaFree(g->cell_start);
+    cudaFree(g->cell_list);
+    cudaFree(g->q_cell);
+    cudaFree(g->q_rank);
+    cudaFree(g->q_perm);
+    cudaFree(g->q_count);
+    cudaFree(g->scan_tmp);
+    delete g;
+}
+
+extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32_t order, vrc_grid** out,
+                                     void* stream) {
+    if (!v || !out || n < 0 || (order != 1 && order != 2)) return VRC_ERR_INVALID;
+    if (n > 0 && (!v->pos || !v->radius || !v->L || !v->grad || (order == 2 && !v->hess))) return VRC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    *out = nullptr;
+    vrc_grid* g = new vrc_grid();
+    g->n = n;
+    g->order = order;
+    // cell size: about a quarter of the median radius, at most 64 cells per axis
+    int G = 1;
+    if (n > 0) {
+        std::vector<float> R(n);
+        if (cudaMemcpyAsync(R.data(), v->radius, sizeof(float) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            vrc_destroy_grid(g);
+            return VRC_ERR_CUDA;
+        }
+        std::nth_element(R.begin(), R.begin() + n / 2, R.end());
+        float med = R[n / 2];
+        if (!(med > 0.f) || !std::isfinite(med)) med = 0.1f;
+        G = (int)std::ceil(4.0f / med);
+        G = std::max(1, std::min(64, G));
+    }
+    g->G = G;
+    int ncell = G * G * G;
+    int nblk = (ncell + 1 + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    int rc = VRC_OK;
+    if ((rc = dev_alloc(&g->rec, 4 * (size_t)n)) || (rc = dev_alloc(&g->hess, order == 2 ? 5 * (size_t)n : 1)) ||
+        (rc = dev_alloc(&g->cell_start, (size_t)ncell + 1)) || (rc = dev_alloc(&g->q_count, (size_t)ncell + 1)) ||
+        (rc = dev_alloc(&g->scan_tmp, (size_t)nblk + 1))) {
+        vrc_destroy_grid(g);
+        return rc;
+    }
+    if (n > 0) {
+        int tb = 256, nbk = (n + tb - 1) / tb;
+        k_pack<<<nbk, tb, 0, st>>>(*v, n, order, g->rec, g->hess);
+        cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
+        k_insert<false><<<nbk, tb, 0, st>>>(g->rec, n, G, g->q_count, nullptr, nullptr);
+        exclusive_scan(g->q_count, ncell, g->cell_start, g->scan_tmp, st);
+        int total = 0;
+        if (cudaMemcpyAsync(&total, g->cell_start + ncell, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            vrc_destroy_grid(g);
+            return VRC_ERR_CUDA;
+        }
+        g->entries = total;
+        if ((rc = dev_alloc(&g->cell_list, (size_t)total))) {
+            vrc_destroy_grid(g);
+            return rc;
+        }
+        cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
+        k_insert<true><<<nbk, tb, 0, st>>>(g->rec, n, G, g->q_count, g->cell_start, g->cell_list);
+        k_sort_lists<<<(ncell + 127) / 128, 128, 0, st>>>(g->cell_start, ncell, g->cell_list);
+    } else {
+        cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);
+        if ((rc = dev_alloc(&g->cell_list, 1))) {
+            vrc_destroy_grid(g);
+            return rc;
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        vrc_destroy_grid(g);
+        return VRC_ERR_CUDA;
+    }
+    *out = g;
+    return VRC_OK;
+}
+
+extern "C" int vrc_query_inscatter(const vrc_grid* gc, const float* d_q, int32_t nq, float* d_rgb,
+                                   int32_t* d_status, void* stream) {
+    if (!gc || nq < 0) return VRC_ERR_INVALID;
+    if (nq == 0) return VRC_OK;
+    if (!d_q || !d_rgb || !d_status) return VRC_ERR_INVALID;
+    vrc_grid* g = const_cast<vrc_grid*>(gc);   // query scratch lives in the grid object
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->q_cap < nq) {
+        cudaFree(g->q_cell);
+        cudaFree(g->q_rank);
+        cudaFree(g->q_perm);
+        g->q_cell = g->q_rank = g->q_perm = nullptr;
+        g->q_cap = 0;
+        if (dev_alloc(&g->q_cell, nq) || dev_alloc(&g->q_rank, nq) || dev_alloc(&g->q_perm, nq)) return VRC_ERR_OOM;
+        g->q_cap = nq;
+    }
+    int G = g->G, ncell = G * G * G;
+    int tb = 256, nbk = (nq + tb - 1) / tb;
+    VRC_CUDA_CHECK(cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st));
+    k_bin_queries<<<nbk, tb, 0, st>>>(d_q, nq, G, g->q_cell, g->q_rank, g->q_count);
+    // reuse cell_start-sized scratch: the query offsets go to q_count's scan in place
+    int rc = exclusive_scan(g->q_count, ncell, g->q_count, g->scan_tmp, st);
+    if (rc) return rc;
+    k_scatter_queries<<<nbk, tb, 0, st>>>(g->q_cell, g->q_rank, g->q_count, nq, g->q_perm);
+    if (g->order == 2)
+        k_query<2><<<nbk, tb, 0, st>>>(g->rec, g->hess, g->cell_start, g->cell_list, G, d_q, g->q_perm, nq, d_rgb,
+                                       d_status);
+    else
+        k_query<1><<<nbk, tb, 0, st>>>(g->rec, g->hess, g->cell_start, g->cell_list, G, d_q, g->q_perm, nq, d_rgb,
+                                       d_status);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}

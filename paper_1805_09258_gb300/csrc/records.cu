@@ -1,0 +1,689 @@
+// records.cu -- cache records: in-scattered radiance, occlusion-aware gradient and
+// Hessian, and validity radius (Secs. 4-5, App. A and App. C of Marco et al. 2018).
+//
+// One thread block computes one record at a time (persistent blocks pull record ids
+// from a work counter).  The record's stratified ray set is processed in chunks of
+// bands so that the vertex ring of a chunk fits in shared memory:
+//   1. primary phase   trace every ray of the chunk (closest hit); surface radiance at
+//                      each hit with a shadow ray per light; Monte Carlo surface term.
+//   2. surface shell   every cell of the chunk's triangulation at the hit points.
+//   3. medium shells   for t_k = (k - 1/2) dt: vertex phase (a shadow ray from every
+//                      unclamped vertex; vertices beyond their hit sit on the hit with
+//                      zero radiance), Monte Carlo medium term, then the cell phase.
+// Each cell yields 32 numbers (L, grad L, H L for 3 channels, the luminance-Hessian
+// norm and a degeneracy flag) in FP32; a warp-transposed butterfly reduces 32 cells
+// so that lane l owns the sum of value l, which it adds to a Neumaier-compensated
+// accumulator (surface shell and medium shells kept apart).  The block's 32 sums are
+// combined at the end; one thread then solves the 3x3 luminance-Hessian eigenproblem
+// in FP64 and sets the radius.
+#include <cmath>
+#include <cstdio>
+
+#include "vrc_internal.cuh"
+
+namespace {
+
+struct RecArgs {
+    const float* pos;
+    int n;
+    const int* n_bands;          // nullable: per-record bands, bins = 2 * bands
+    int nb0, ns0;                // uniform bands / bins
+    float dt, eps;
+    float3 wo;
+    uint64_t seed;
+    int ff_signed;
+    float r_min, r_max;
+    long long rec_base;
+    vrc_records_view out;
+    int chunk_bands;             // bands per chunk
+    int cap;                     // shared-memory vertex capacity per chunk
+    int* counter;                // work counter (reset before the launch)
+};
+
+__device__ __forceinline__ void neumaier(float& s, float& c, float x) {
+    float t = s + x;
+    if (fabsf(s) >= fabsf(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+// lane l of the warp receives the sum over the warp of v[l] (v is 32 values per lane)
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            float send = up ? v[i] : v[i + s];
+            float keep = up ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+// ----------------------------------------------------------------- vertex radiance
+// Medium vertex: single scattering from the point lights (bounce limit, Sec. 6).
+__device__ float3 medium_radiance(const DevScene& sc, float3 y, float3 d) {
+    float3 L = f3(0.f, 0.f, 0.f);
+    for (int l = 0; l < sc.n_lights; ++l) {
+        float3 lv = sc.lpos[l] - y;
+        float d2 = dot3(lv, lv);
+        float dist = sqrtf(d2);
+        float3 lh = lv * (1.0f / dist);
+        float th;
+        if (bvh_trace<true>(sc, y, lh, VRC_TMIN, dist, &th) >= 0) continue;
+        float f = hg_dev(dot3(lh, d), sc.g);      // light p_L -> y, then y -> x along -d
+        float w = f * __expf(-sc.sigma_t * dist) / d2;
+        L = L + sc.lI[l] * w;
+    }
+    return L;
+}
+
+// Surface vertex: Lambertian, two-sided (the light must be on the record's side),
+// plus emission.
+__device__ float3 surface_radiance(const DevScene& sc, int prim, float3 y, float3 d) {
+    float4 n4 = __ldg(&sc.prim[3 * prim]);
+    float4 al = __ldg(&sc.prim[3 * prim + 1]);
+    float4 em = __ldg(&sc.prim[3 * prim + 2]);
+    float3 n = f3(n4.x, n4.y, n4.z);
+    if (dot3(n, d) > 0.f) n = n * -1.0f;
+    float3 L = f3(em.x, em.y, em.z);
+    for (int l = 0; l < sc.n_lights; ++l) {
+        float3 lv = sc.lpos[l] - y;
+        float d2 = dot3(lv, lv);
+        float dist = sqrtf(d2);
+        float cs = dot3(n, lv) / dist;
+        if (cs <= 0.f) continue;
+        float3 o = y + n * 1e-5f;
+        float3 lo = sc.lpos[l] - o;
+        float dl = sqrtf(dot3(lo, lo));
+        float th;
+        if (bvh_trace<true>(sc, o, lo * (1.0f / dl), VRC_TMIN, dl, &th) >= 0) continue;
+        float w = cs * __expf(-sc.sigma_t * dist) / (d2 * VRC_PI_F);
+        L = L + f3(al.x * sc.lI[l].x, al.y * sc.lI[l].y, al.z * sc.lI[l].z) * w;
+    }
+    return L;
+}
+
+// ----------------------------------------------------------------- one cell
+// Cell j with vertices r_q = y_q - x (q = 0..2) at ray parameters t_q and radiance
+// Lo_q.  Writes the 32 values: L_j (3), grad L_j (3 x 3), H L_j (3 x 6), the Frobenius
+// norm of the luminance Hessian, and 1 in v[31] for a degenerate cell (A = B = 0).
+// Returns the number of tied furthest vertices evaluated (0: dark or degenerate cell).
+//   L_j = f(w_c) Omega_j (1/m) sum_{q tied furthest} Lo_q T(|r_q|)
+// Omega = 2 atan2(A, B) (Van Oosterom-Strackee) with A = r1 . (r2 x r3),
+// B = r1 r2 r3 + (r1.r2) r3 + (r2.r3) r1 + (r1.r3) r2, grad A = -(r2-r1) x (r3-r1),
+// H A = 0.  Here grad B = -sum_i c_i r_i with c_i = (rho_j rho_k + r_j.r_k)/rho_i + rho_j
+// + rho_k, and H B = (sum c_i) I - sum_i r_i grad c_i^T; the Hessian of Omega is the
+// symmetric form 2[-A HB/D - (2/D^2)(AB(aa^T - bb^T) + (B^2-A^2)/2 (ab^T + ba^T))].
+__device__ __forceinline__ int cell_eval(const float3 (&r)[3], const float (&t)[3], const float3 (&Lo)[3],
+                                         float sigma_t, float g, float3 wo, int ff_signed, float (&v)[32]) {
+    float tmx = fmaxf(t[0], fmaxf(t[1], t[2]));
+    bool far0 = t[0] == tmx, far1 = t[1] == tmx, far2 = t[2] == tmx;
+    bool lit = (far0 && (Lo[0].x != 0.f || Lo[0].y != 0.f || Lo[0].z != 0.f)) ||
+               (far1 && (Lo[1].x != 0.f || Lo[1].y != 0.f || Lo[1].z != 0.f)) ||
+               (far2 && (Lo[2].x != 0.f || Lo[2].y != 0.f || Lo[2].z != 0.f));
+    if (!lit) return 0;
+    // ---- solid angle and its derivatives
+    float rho[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) rho[q] = sqrtf(dot3(r[q], r[q]));
+    float3 e1 = r[1] - r[0], e2 = r[2] - r[0];
+    float3 nrm = cross3(e1, e2);
+    float A = dot3(r[0], nrm);
+    float3 a = nrm * -1.0f;
+    if (!ff_signed && A < 0.f) { A = -A; a = nrm; }
+    float d01 = dot3(r[0], r[1]), d12 = dot3(r[1], r[2]), d02 = dot3(r[0], r[2]);
+    float B = fmaf(rho[0] * rho[1], rho[2], fmaf(d01, rho[2], fmaf(d12, rho[0], d02 * rho[1])));
+    float D = fmaf(A, A, B * B);
+    if (!(D > 1e-36f)) { v[31] = 1.0f; return 0; }
+    float c[3];
+    float3 gc[3];
+    float dd[3] = {d12, d02, d01};   // r_j . r_k for the other two of i
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3, k = (i + 2) % 3;
+        float ir = 1.0f / rho[i];
+        float P = fmaf(rho[j], rho[k], dd[i]);
+        c[i] = fmaf(P, ir, rho[j] + rho[k]);
+        float irj = 1.0f / rho[j], irk = 1.0f / rho[k];
+        // grad c_i = (-rho_k u_j - rho_j u_k - r_j - r_k)/rho_i + P u_i/rho_i^2 - u_j - u_k
+        float aj = -(rho[k] * irj + 1.0f) * ir - irj;   // coefficient of r_j
+        float ak = -(rho[j] * irk + 1.0f) * ir - irk;   // coefficient of r_k
+        float ai = P * ir * ir * ir;                    // coefficient of r_i
+        gc[i] = r[j] * aj + r[k] * ak + r[i] * ai;
+    }
+    float3 b = (r[0] * c[0] + r[1] * c[1] + r[2] * c[2]) * -1.0f;
+    float csum = c[0] + c[1] + c[2];
+    // H B, 6 unique entries (xx, xy, xz, yy, yz, zz)
+    float HB[6];
+    HB[0] = csum - (r[0].x * gc[0].x + r[1].x * gc[1].x + r[2].x * gc[2].x);
+    HB[1] = -(r[0].x * gc[0].y + r[1].x * gc[1].y + r[2].x * gc[2].y);
+    HB[2] = -(r[0].x * gc[0].z + r[1].x * gc[1].z + r[2].x * gc[2].z);
+    HB[3] = csum - (r[0].y * gc[0].y + r[1].y * gc[1].y + r[2].y * gc[2].y);
+    HB[4] = -(r[0].y * gc[0].z + r[1].y * gc[1].z + r[2].y * gc[2].z);
+    HB[5] = csum - (r[0].z * gc[0].z + r[1].z * gc[1].z + r[2].z * gc[2].z);
+    float iD = 1.0f / D;
+    float Om = 2.0f * atan2f(A, B);
+    float3 gO = (a * B - b * A) * (2.0f * iD);
+    float k1 = -2.0f * A * iD;                       // coefficient of H B
+    float k2 = -4.0f * iD * iD * A * B;              // of (aa^T - bb^T)
+    float k3 = -2.0f * iD * iD * (B * B - A * A);    // of (ab^T + ba^T)
+    float HO[6];
+    HO[0] = k1 * HB[0] + k2 * (a.x * a.x - b.x * b.x) + k3 * 2.0f * a.x * b.x;
+    HO[1] = k1 * HB[1] + k2 * (a.x * a.y - b.x * b.y) + k3 * (a.x * b.y + b.x * a.y);
+    HO[2] = k1 * HB[2] + k2 * (a.x * a.z - b.x * b.z) + k3 * (a.x * b.z + b.x * a.z);
+    HO[3] = k1 * HB[3] + k2 * (a.y * a.y - b.y * b.y) + k3 * 2.0f * a.y * b.y;
+    HO[4] = k1 * HB[4] + k2 * (a.y * a.z - b.y * b.z) + k3 * (a.y * b.z + b.y * a.z);
+    HO[5] = k1 * HB[5] + k2 * (a.z * a.z - b.z * b.z) + k3 * 2.0f * a.z * b.z;
+    // ---- phase function along the direction from the cell centroid to x
+    float fv, gf[3] = {0.f, 0.f, 0.f}, Hf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (g == 0.0f) {
+        fv = 0.25f / VRC_PI_F;
+    } else {
+        float3 w = (r[0] + r[1] + r[2]) * (-1.0f / 3.0f);
+        float iw = rsqrtf(dot3(w, w));
+        float3 wi = w * iw;
+        float mu = dot3(wi, wo);
+        float q = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
+        float rq = rsqrtf(q);
+        float cg = (1.0f - g * g) * (0.25f / VRC_PI_F);
+        float rq3 = rq * rq * rq;
+        fv = cg * rq3;
+        float f1 = 3.0f * g * cg * rq3 * rq * rq;             // df/dmu
+        float f2 = 5.0f * g * f1 * rq * rq;                   // d2f/dmu2
+        float3 gm = (wo - wi * mu) * iw;                      // grad mu
+        float iw2 = iw * iw;
+        // H mu = (-wo wi^T - wi wo^T - mu I + 3 mu wi wi^T) / |w|^2
+        float Hm[6] = {(-2.f * wo.x * wi.x - mu + 3.f * mu * wi.x * wi.x) * iw2,
+                       (-wo.x * wi.y - wi.x * wo.y + 3.f * mu * wi.x * wi.y) * iw2,
+                       (-wo.x * wi.z - wi.x * wo.z + 3.f * mu * wi.x * wi.z) * iw2,
+                       (-2.f * wo.y * wi.y - mu + 3.f * mu * wi.y * wi.y) * iw2,
+                       (-wo.y * wi.z - wi.y * wo.z + 3.f * mu * wi.y * wi.z) * iw2,
+                       (-2.f * wo.z * wi.z - mu + 3.f * mu * wi.z * wi.z) * iw2};
+        gf[0] = f1 * gm.x; gf[1] = f1 * gm.y; gf[2] = f1 * gm.z;
+        Hf[0] = f2 * gm.x * gm.x + f1 * Hm[0];
+        Hf[1] = f2 * gm.x * gm.y + f1 * Hm[1];
+        Hf[2] = f2 * gm.x * gm.z + f1 * Hm[2];
+        Hf[3] = f2 * gm.y * gm.y + f1 * Hm[3];
+        Hf[4] = f2 * gm.y * gm.z + f1 * Hm[4];
+        Hf[5] = f2 * gm.z * gm.z + f1 * Hm[5];
+    }
+    // ---- reduced radiance at the tied furthest vertices, product rule, RGB scatter
+    float inv_m = 1.0f / (float)((int)far0 + (int)far1 + (int)far2);
+    float HY[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        bool fq = q == 0 ? far0 : (q == 1 ? far1 : far2);
+        if (!fq) continue;
+        float ir = 1.0f / rho[q];
+        float3 u = r[q] * ir;
+        float T = __expf(-sigma_t * rho[q]);
+        float st_T = sigma_t * T;
+        float3 gT = u * st_T;                              // grad T = sigma_t T (y - x)/|y - x|
+        float h1 = st_T * (ir + sigma_t), h0 = -st_T * ir; // H T = st T [(1/rho + st) u u^T - I/rho]
+        float HT[6] = {h1 * u.x * u.x + h0, h1 * u.x * u.y, h1 * u.x * u.z,
+                       h1 * u.y * u.y + h0, h1 * u.y * u.z, h1 * u.z * u.z + h0};
+        // P = Omega T
+        float P = Om * T;
+        float gP[3] = {T * gO.x + Om * gT.x, T * gO.y + Om * gT.y, T * gO.z + Om * gT.z};
+        float gOa[3] = {gO.x, gO.y, gO.z}, gTa[3] = {gT.x, gT.y, gT.z};
+        float HP[6];
+        const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+            HP[e] = T * HO[e] + gTa[ii[e]] * gOa[jj[e]] + gOa[ii[e]] * gTa[jj[e]] + Om * HT[e];
+        // G = f P
+        float G = fv * P;
+        float gG[3], HG[6];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) gG[e] = P * gf[e] + fv * gP[e];
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+            HG[e] = P * Hf[e] + gP[ii[e]] * gf[jj[e]] + gf[ii[e]] * gP[jj[e]] + fv * HP[e];
+        float3 L = Lo[q] * inv_m;
+        float Lc[3] = {L.x, L.y, L.z};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            v[ch] = fmaf(Lc[ch], G, v[ch]);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) v[3 + 3 * ch + e] = fmaf(Lc[ch], gG[e], v[3 + 3 * ch + e]);
+#pragma unroll
+            for (int e = 0; e < 6; ++e) v[12 + 6 * ch + e] = fmaf(Lc[ch], HG[e], v[12 + 6 * ch + e]);
+        }
+        float Y = 0.2126f * L.x + 0.7152f * L.y + 0.0722f * L.z;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) HY[e] = fmaf(Y, HG[e], HY[e]);
+    }
+    v[30] = sqrtf(HY[0] * HY[0] + HY[3] * HY[3] + HY[5] * HY[5] +
+                  2.0f * (HY[1] * HY[1] + HY[2] * HY[2] + HY[4] * HY[4]));
+    return (int)far0 + (int)far1 + (int)far2;
+}
+
+// ----------------------------------------------------------------- FP64 eigenvalues
+// Symmetric 3x3 eigenvalues by the trigonometric closed form (Smith, CACM 1961).
+__device__ void eig3_sym(const double h[6], double lam[3]) {
+    double a00 = h[0], a01 = h[1], a02 = h[2], a11 = h[3], a12 = h[4], a22 = h[5];
+    double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    double q = (a00 + a11 + a22) / 3.0;
+    double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + 2.0 * p1;
+    if (p2 <= 0.0) {
+        lam[0] = lam[1] = lam[2] = q;
+        return;
+    }
+    double p = sqrt(p2 / 6.0);
+    double ip = 1.0 / p;
+    double b00 = (a00 - q) * ip, b11 = (a11 - q) * ip, b22 = (a22 - q) * ip;
+    double b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
+    double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+    double rr = fmin(1.0, fmax(-1.0, 0.5 * det));
+    double phi = acos(rr) / 3.0;
+    double e1 = q + 2.0 * p * cos(phi);
+    double e3 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+    double e2 = 3.0 * q - e1 - e3;
+    lam[0] = e3;
+    lam[1] = e2;
+    lam[2] = e1;
+    if (lam[1] < lam[0]) { double tt = lam[0]; lam[0] = lam[1]; lam[1] = tt; }
+    if (lam[2] < lam[1]) { double tt = lam[1]; lam[1] = lam[2]; lam[2] = tt; }
+    if (lam[1] < lam[0]) { double tt = lam[0]; lam[0] = lam[1]; lam[1] = tt; }
+}
+
+// ----------------------------------------------------------------- the kernel
+template <int NT>
+__global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
+    constexpr int NW = NT / 32;
+    extern __shared__ float4 smem4[];
+    float4* ray = smem4;                                     // (d, t_end) per chunk vertex
+    float* Lr = reinterpret_cast<float*>(ray + a.cap);
+    float* Lg = Lr + a.cap;
+    float* Lb = Lg + a.cap;
+    float* red = Lb + a.cap;                                 // [NW][32][4]
+    float* mcs = red + NW * 32 * 4;                          // [NW][12]
+    float* tot = mcs + NW * 12;                              // [128]
+    int* misc = reinterpret_cast<int*>(tot + 128);           // [4]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float sigma_t = sc.sigma_t, g = sc.g;
+    __shared__ int s_rec;
+
+    for (;;) {
+        if (tid == 0) s_rec = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int rec = s_rec;
+        if (rec >= a.n) break;
+        const int nb = a.n_bands ? a.n_bands[rec] : a.nb0;
+        const int ns = a.n_bands ? 2 * nb : a.ns0;
+        const int N = nb * ns;
+        const long long rid = a.rec_base + rec;
+        const float3 x = f3(a.pos[3 * rec], a.pos[3 * rec + 1], a.pos[3 * rec + 2]);
+        const float wmc = 4.0f * VRC_PI_F / (float)N;
+        float acc_s = 0.f, cmp_s = 0.f, acc_m = 0.f, cmp_m = 0.f;     // lane-owned cell sums
+        float mc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mcc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int kmax_rec = 0;
+        int lit_cells = 0, far_evals = 0;                    // lane 0 of each warp counts its warp's cells
+        const int CB = a.chunk_bands < nb ? a.chunk_bands : nb;
+
+        for (int r0 = 0; r0 < nb; r0 += CB) {
+            const int r1 = min(r0 + CB, nb);               // owned rows [r0, r1)
+            const int r1e = min(r1, nb - 1);               // plus the next row (borrowed)
+            const int rows = r1e - r0 + 1;
+            const bool north = r0 == 0, south = r1 == nb;
+            const int nvert = rows * ns + 2;
+            const int PN = rows * ns, PS = rows * ns + 1;
+            if (tid == 0) misc[0] = 0;
+            __syncthreads();
+            // ---------------- primary phase
+            float tmax_loc = 0.f;
+            for (int lv = tid; lv < nvert; lv += NT) {
+                int gv, row = 0;
+                bool pole = lv >= rows * ns;
+                if (!pole) {
+                    row = r0 + lv / ns;
+                    gv = row * ns + (lv - (lv / ns) * ns);
+                } else {
+                    gv = lv == PN ? N : N + 1;
+                }
+                float3 d = ray_direction_dev(a.seed, rid, gv, nb, ns);
+                float th;
+                int prim = bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
+                float3 Lo = f3(0.f, 0.f, 0.f);
+                float te;
+                if (prim >= 0) {
+                    te = th;
+                    Lo = surface_radiance(sc, prim, x + d * te, d);
+                } else {
+                    te = cube_exit_dev(x, d);
+                }
+                ray[lv] = make_float4(d.x, d.y, d.z, te);
+                Lr[lv] = Lo.x;
+                Lg[lv] = Lo.y;
+                Lb[lv] = Lo.z;
+                tmax_loc = fmaxf(tmax_loc, te);
+                bool owned = !pole && row < r1;
+                if (owned && prim >= 0) {
+                    float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * te);
+                    neumaier(mc[0], mcc[0], w * Lo.x);
+                    neumaier(mc[1], mcc[1], w * Lo.y);
+                    neumaier(mc[2], mcc[2], w * Lo.z);
+                }
+                if (a.out.hit_prim && (owned || (pole && ((lv == PN && north) || (lv == PS && south))))) {
+                    size_t o = (size_t)rec * a.out.dbg_stride + gv;
+                    a.out.hit_prim[o] = prim;
+                    a.out.hit_t[o] = te;
+                }
+            }
+            atomicMax(&misc[0], __float_as_int(tmax_loc));   // non-negative floats order as ints
+            __syncthreads();
+            const int K = (int)ceilf(__int_as_float(misc[0]) / a.dt);
+            kmax_rec = max(kmax_rec, K);
+            // cells of this chunk
+            const int nq = r1e - r0;                         // quad bands with upper row in [r0, r1e)
+            const int ncell = (north ? ns : 0) + 2 * ns * nq + (south ? ns : 0);
+            for (int k = 0; k <= K; ++k) {
+                const float tk = ((float)k - 0.5f) * a.dt;
+                if (k > 0) {
+                    // ---------------- vertex phase of medium shell k
+                    for (int lv = tid; lv < nvert; lv += NT) {
+                        float4 rv = ray[lv];
+                        float3 d = f3(rv.x, rv.y, rv.z);
+                        float3 Lo = f3(0.f, 0.f, 0.f);
+                        if (tk < rv.w) {
+                            Lo = medium_radiance(sc, x + d * tk, d);
+                            bool pole = lv >= rows * ns;
+                            bool owned = !pole && (r0 + lv / ns) < r1;
+                            if (owned) {
+                                float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * tk);
+                                neumaier(mc[3], mcc[3], w * Lo.x);
+                                neumaier(mc[4], mcc[4], w * Lo.y);
+                                neumaier(mc[5], mcc[5], w * Lo.z);
+                            }
+                        }
+                        Lr[lv] = Lo.x;
+                        Lg[lv] = Lo.y;
+                        Lb[lv] = Lo.z;
+                    }
+                    __syncthreads();
+                }
+                // ---------------- cell phase of shell k
+                const int nround = (ncell + 31) & ~31;
+                for (int base = warp * 32; base < nround; base += NT) {
+                    float v[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = 0.f;
+                    int c = base + lane;
+                    int m = 0;
+                    if (c < ncell) {
+                        int vi[3];
+                        int cc = c;
+                        if (north && cc < ns) {
+                            vi[0] = PN; vi[1] = cc; vi[2] = (cc + 1) % ns;
+                        } else {
+                            if (north) cc -= ns;
+                            if (cc < 2 * ns * nq) {
+                                int qd = cc >> 1, ri = qd / ns, j = qd - ri * ns, j1 = (j + 1) % ns;
+                                int v00 = ri * ns + j, v01 = ri * ns + j1, v10 = (ri + 1) * ns + j, v11 = (ri + 1) * ns + j1;
+                                if ((cc & 1) == 0) { vi[0] = v00; vi[1] = v10; vi[2] = v11; }
+                                else { vi[0] = v00; vi[1] = v11; vi[2] = v01; }
+                            } else {
+                                cc -= 2 * ns * nq;
+                                int rl = (nb - 1 - r0) * ns;
+                                vi[0] = PS; vi[1] = rl + (cc + 1) % ns; vi[2] = rl + cc;
+                            }
+                        }
+                        float3 rr[3], Lo[3];
+                        float tt[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            float4 rv = ray[vi[q]];
+                            float tq = (k == 0 || !(tk < rv.w)) ? rv.w : tk;
+                            tt[q] = tq;
+                            rr[q] = f3(rv.x * tq, rv.y * tq, rv.z * tq);
+                            Lo[q] = f3(Lr[vi[q]], Lg[vi[q]], Lb[vi[q]]);
+                        }
+                        m = cell_eval(rr, tt, Lo, sigma_t, g, a.wo, a.ff_signed, v);
+                    }
+                    if (a.out.n_cells) {
+                        unsigned lit = __ballot_sync(0xffffffffu, m > 0);
+                        int fsum = m;
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+                        if (lane == 0) { lit_cells += __popc(lit); far_evals += fsum; }
+                    }
+                    float mine = warp_transpose_reduce(v, lane);
+                    if (k == 0) neumaier(acc_s, cmp_s, mine);
+                    else neumaier(acc_m, cmp_m, mine);
+                }
+                __syncthreads();
+            }
+        }
+        // ---------------- block reduction and outputs
+        red[(warp * 32 + lane) * 4 + 0] = acc_s;
+        red[(warp * 32 + lane) * 4 + 1] = cmp_s;
+        red[(warp * 32 + lane) * 4 + 2] = acc_m;
+        red[(warp * 32 + lane) * 4 + 3] = cmp_m;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            float s = mc[e] + mcc[e];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) mcs[warp * 12 + e] = s;
+        }
+        if (tid == 0) { misc[1] = 0; misc[3] = 0; }
+        __syncthreads();
+        if (lane == 0 && a.out.n_cells) { atomicAdd(&misc[1], lit_cells); atomicAdd(&misc[3], far_evals); }
+        __syncthreads();
+        const float wms = sc.sigma_s * a.dt;                 // 1 / pdf of a medium shell
+        if (warp == 0) {
+            float s_s = 0.f, c_s = 0.f, s_m = 0.f, c_m = 0.f;
+            for (int w = 0; w < NW; ++w) {
+                neumaier(s_s, c_s, red[(w * 32 + lane) * 4 + 0]);
+                neumaier(s_s, c_s, red[(w * 32 + lane) * 4 + 1]);
+                neumaier(s_m, c_m, red[(w * 32 + lane) * 4 + 2]);
+                neumaier(s_m, c_m, red[(w * 32 + lane) * 4 + 3]);
+            }
+            float vs = s_s + c_s, vm = (s_m + c_m) * wms;
+            tot[lane] = vs + vm;        // total
+            tot[32 + lane] = vs;        // surface shell
+            tot[64 + lane] = vm;        // medium shells
+            if (lane < 6) {
+                float s = 0.f, cpn = 0.f;
+                for (int w = 0; w < NW; ++w) neumaier(s, cpn, mcs[w * 12 + lane]);
+                tot[96 + lane] = s + cpn;
+            }
+        }
+        __syncthreads();
+        const vrc_records_view& o = a.out;
+        if (tid < 30) {
+            // value index -> output slot: 0..2 L_ff, 3..11 grad [c][axis], 12..29 hess [c][6]
+            float vt = tot[tid], vs = tot[32 + tid], vm = tot[64 + tid];
+            if (tid < 3) {
+                if (o.L_ff) o.L_ff[3 * rec + tid] = vt;
+            } else if (tid < 12) {
+                int e = tid - 3;
+                o.grad[9 * rec + e] = vt;
+                if (o.grad_ss) o.grad_ss[9 * rec + e] = vs;
+                if (o.grad_ms) o.grad_ms[9 * rec + e] = vm;
+            } else {
+                int e = tid - 12;
+                o.hess[18 * rec + e] = vt;
+                if (o.hess_ss) o.hess_ss[18 * rec + e] = vs;
+                if (o.hess_ms) o.hess_ms[18 * rec + e] = vm;
+            }
+        } else if (tid >= 32 && tid < 35) {
+            int ch = tid - 32;
+            float ls = tot[96 + ch], lm = tot[99 + ch] * wms;
+            o.L[3 * rec + ch] = ls + lm;
+            if (o.L_ss) o.L_ss[3 * rec + ch] = ls;
+            if (o.L_ms) o.L_ms[3 * rec + ch] = lm;
+            o.pos[3 * rec + ch] = ch == 0 ? x.x : (ch == 1 ? x.y : x.z);
+        } else if (tid == 64) {
+            // luminance Hessian, FP64 eigenvalues and radius (Eq. radiusAniso3D)
+            const double Y[3] = {0.2126, 0.7152, 0.0722};
+            double h[6];
+            bool finite = true;
+            for (int e = 0; e < 6; ++e) {
+                h[e] = Y[0] * (double)tot[12 + e] + Y[1] * (double)tot[18 + e] + Y[2] * (double)tot[24 + e];
+            }
+            double LY = 0.0;
+            for (int ch = 0; ch < 3; ++ch)
+                LY += Y[ch] * ((double)tot[96 + ch] + (double)tot[99 + ch] * (double)wms);
+            for (int e = 0; e < 32; ++e)
+                if (e != 30 && e != 31 && !isfinite(tot[e])) finite = false;
+            for (int e = 0; e < 6; ++e)
+                if (!isfinite(tot[96 + e])) finite = false;
+            double lam[3];
+            eig3_sym(h, lam);
+            double lmax = fmax(fabs(lam[0]), fmax(fabs(lam[1]), fabs(lam[2])));
+            int status = 0;
+            double R;
+            if (!finite || !isfinite(LY) || !isfinite(lmax)) { status |= VRC_REC_NONFINITE | VRC_REC_CLAMP_LO; R = a.r_min; }
+            else if (!(LY > 0.0)) { status |= VRC_REC_CLAMP_LO; R = a.r_min; }
+            else if (lmax == 0.0) { status |= VRC_REC_CLAMP_HI; R = a.r_max; }
+            else {
+                R = pow(15.0 * LY * (double)a.eps / (4.0 * 3.14159265358979323846 * lmax), 0.2);
+                if (R < a.r_min) { status |= VRC_REC_CLAMP_LO; R = a.r_min; }
+                if (R > a.r_max) { status |= VRC_REC_CLAMP_HI; R = a.r_max; }
+            }
+            if (tot[31] + tot[63] > 0.f) status |= VRC_REC_DEGENERATE;
+            o.radius[rec] = (float)R;
+            o.status[rec] = status;
+            if (o.n_cells) o.n_cells[rec] = misc[1];
+            if (o.n_far) o.n_far[rec] = misc[3];
+            if (o.n_shells) o.n_shells[rec] = kmax_rec;
+            if (o.eig) {
+                o.eig[3 * rec] = (float)lam[0];
+                o.eig[3 * rec + 1] = (float)lam[1];
+                o.eig[3 * rec + 2] = (float)lam[2];
+            }
+            if (o.kappa) {
+                double hn = sqrt(h[0] * h[0] + h[3] * h[3] + h[5] * h[5] + 2.0 * (h[1] * h[1] + h[2] * h[2] + h[4] * h[4]));
+                o.kappa[rec] = (float)((double)tot[30] / hn);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t record_smem_bytes(int cap, int nt) {
+    int nw = nt / 32;
+    return (size_t)cap * 16 + (size_t)cap * 12 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4;
+}
+
+template <int NT>
+int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st) {
+    auto kfn = k_records<NT>;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return VRC_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, smem) != cudaSuccess || per_sm < 1)
+        return VRC_ERR_UNSUPPORTED;
+    if (s->tuning.blocks_per_sm > 0 && s->tuning.blocks_per_sm < per_sm) per_sm = s->tuning.blocks_per_sm;
+    int grid = per_sm * s->sm_count;
+    if (grid > a.n) grid = a.n;
+    if (grid < 1) grid = 1;
+    kfn<<<grid, NT, smem, st>>>(s->dev, a);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int vrc_set_record_tuning(vrc_scene* s, const vrc_record_tuning* t) {
+    if (!s || !t) return VRC_ERR_INVALID;
+    if (t->threads != 0 && t->threads != 128 && t->threads != 256 && t->threads != 512) return VRC_ERR_INVALID;
+    if (t->chunk_bands < 0 || t->blocks_per_sm < 0) return VRC_ERR_INVALID;
+    s->tuning = *t;
+    return VRC_OK;
+}
+
+extern "C" int vrc_get_record_tuning(const vrc_scene* s, vrc_record_tuning* t) {
+    if (!s || !t) return VRC_ERR_INVALID;
+    *t = s->tuning;
+    return VRC_OK;
+}
+
+extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, const int32_t* d_n_bands,
+                                   const vrc_record_params* p, const vrc_records_view* out, void* stream) {
+    if (!s || !p || !out || n < 0) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    if (!d_pos || !out->L || !out->grad || !out->hess || !out->radius || !out->status || !out->pos)
+        return VRC_ERR_INVALID;
+    int nb = p->n_bands, ns = d_n_bands ? 2 * p->n_bands : p->n_bins;
+    if (nb < 1 || ns < 3 || !(p->dt > 0.f) || !(p->eps > 0.f) || !(p->r_min > 0.f) || !(p->r_max >= p->r_min))
+        return VRC_ERR_INVALID;
+    if (nb > 256 || ns > 512) return VRC_ERR_UNSUPPORTED;
+    if ((out->hit_prim != nullptr) != (out->hit_t != nullptr)) return VRC_ERR_INVALID;
+    if (out->hit_prim && out->dbg_stride < nb * ns + 2) return VRC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int nt = s->tuning.threads ? s->tuning.threads : 256;
+    // bands per chunk: as many as fit a shared-memory budget (about two blocks per SM)
+    int cb = s->tuning.chunk_bands;
+    if (cb <= 0) {
+        cb = nb;
+        while (cb > 1 && record_smem_bytes((cb + 1) * ns + 2, nt) > 110 * 1024) cb = (cb + 1) / 2;
+    }
+    if (cb > nb) cb = nb;
+    int cap = (cb + 1) * ns + 2;
+    size_t smem = record_smem_bytes(cap, nt);
+    if (smem > 227 * 1024) return VRC_ERR_UNSUPPORTED;
+    RecArgs a;
+    a.pos = d_pos;
+    a.n = n;
+    a.n_bands = d_n_bands;
+    a.nb0 = nb;
+    a.ns0 = ns;
+    a.dt = p->dt;
+    a.eps = p->eps;
+    a.wo = make_float3(p->omega_o[0], p->omega_o[1], p->omega_o[2]);
+    a.seed = p->seed;
+    a.ff_signed = p->ff_signed;
+    a.r_min = p->r_min;
+    a.r_max = p->r_max;
+    a.rec_base = p->rec_base;
+    a.out = *out;
+    a.chunk_bands = cb;
+    a.cap = cap;
+    a.counter = s->d_counter;
+    VRC_CUDA_CHECK(cudaMemsetAsync(s->d_counter, 0, sizeof(int), st));
+    switch (nt) {
+        case 128: return launch_records<128>(s, a, smem, st);
+        case 512: return launch_records<512>(s, a, smem, st);
+        default: return launch_records<256>(s, a, smem, st);
+    }
+}
+
+extern "C" int vrc_compute_records_host(vrc_scene* s, const float* h_pos, int32_t n, const vrc_record_params* p,
+                                        float* h_L, float* h_grad, float* h_hess, float* h_radius,
+                                        int32_t* h_status) {
+    if (!s || !p || n < 0 || (n > 0 && !h_pos)) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    // staging layout (floats per record): pos 3, L 3, grad 9, hess 18, radius 1, status 1, pos copy 3
+    const size_t per = 38;
+    size_t need = per * (size_t)n;
+    if (s->h_stage_floats < need) {
+        cudaFree(s->h_stage_dev);
+        s->h_stage_dev = nullptr;
+        s->h_stage_floats = 0;
+        if (cudaMalloc((void**)&s->h_stage_dev, need * sizeof(float)) != cudaSuccess) return VRC_ERR_OOM;
+        s->h_stage_floats = need;
+    }
+    float* base = s->h_stage_dev;
+    float* d_pos = base;
+    vrc_records_view v = {};
+    v.L = base + 3 * (size_t)n;
+    v.grad = base + 6 * (size_t)n;
+    v.hess = base + 15 * (size_t)n;
+    v.radius = base + 33 * (size_t)n;
+    v.status = reinterpret_cast<int32_t*>(base + 34 * (size_t)n);
+    v.pos = base + 35 * (size_t)n;
+    VRC_CUDA_CHECK(cudaMemcpy(d_pos, h_pos, 3 * sizeof(float) * n, cudaMemcpyHostToDevice));
+    int rc = vrc_compute_records(s, d_pos, n, nullptr, p, &v, nullptr);
+    if (rc != VRC_OK) return rc;
+    if (h_L) VRC_CUDA_CHECK(cudaMemcpy(h_L, v.L, 3 * sizeof(float) * n, cudaMemcpyDeviceToHost));
+    if (h_grad) VRC_CUDA_CHECK(cudaMemcpy(h_grad, v.grad, 9 * sizeof(float) * n, cudaMemcpyDeviceToHost));
+    if (h_hess) VRC_CUDA_CHECK(cudaMemcpy(h_hess, v.hess, 18 * sizeof(float) * n, cudaMemcpyDeviceToHost));
+    if (h_radius) VRC_CUDA_CHECK(cudaMemcpy(h_radius, v.radius, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    if (h_status) VRC_CUDA_CHECK(cudaMemcpy(h_status, v.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    VRC_CUDA_CHECK(cudaDeviceSynchronize());
+    return VRC_OK;
+}

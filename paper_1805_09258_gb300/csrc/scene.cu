@@ -1,0 +1,276 @@
+// scene.cu -- scene upload and bounding volume hierarchy (host build, device layout).
+//
+// The paper traces its ray sets with Embree on a CPU (Sec. 6); here the scene lives
+// in HBM as a two-wide BVH built on the host with binned surface-area heuristic
+// splits, traversed by the library's own kernels (vrc_internal.cuh).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "vrc_internal.cuh"
+
+namespace {
+
+struct BTri {
+    float lo[3], hi[3], c[3];
+    int id;
+};
+
+struct HNode {
+    float lo[2][3], hi[2][3];
+    int child[2];
+};
+
+struct Builder {
+    std::vector<BTri> tris;
+    std::vector<HNode> nodes;
+    std::vector<int> order;   // leaf order of original triangle ids
+    int max_depth = 0;
+
+    static void bound(const BTri* t, int n, float lo[3], float hi[3]) {
+        for (int k = 0; k < 3; ++k) { lo[k] = 1e30f; hi[k] = -1e30f; }
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], t[i].lo[k]);
+                hi[k] = std::max(hi[k], t[i].hi[k]);
+            }
+    }
+    static float area(const float lo[3], const float hi[3]) {
+        float dx = std::max(0.f, hi[0] - lo[0]), dy = std::max(0.f, hi[1] - lo[1]), dz = std::max(0.f, hi[2] - lo[2]);
+        return 2.f * (dx * dy + dy * dz + dz * dx);
+    }
+
+    int make_leaf(int begin, int count) {
+        int first = (int)order.size();
+        for (int i = begin; i < begin + count; ++i) order.push_back(tris[i].id);
+        return -(1 + ((first << 3) | (count - 1)));
+    }
+
+    // returns a child code for tris[begin, begin + count)
+    int build(int begin, int count, int depth) {
+        max_depth = std::max(max_depth, depth);
+        if (count <= 2) return make_leaf(begin, count);
+        float clo[3] = {1e30f, 1e30f, 1e30f}, chi[3] = {-1e30f, -1e30f, -1e30f};
+        for (int i = begin; i < begin + count; ++i)
+            for (int k = 0; k < 3; ++k) {
+                clo[k] = std::min(clo[k], tris[i].c[k]);
+                chi[k] = std::max(chi[k], tris[i].c[k]);
+            }
+        const int NB = 16;
+        float best_cost = 1e30f;
+        int best_axis = -1, best_bin = -1;
+        float plo[3], phi[3];
+        bound(&tris[begin], count, plo, phi);
+        float parea = std::max(area(plo, phi), 1e-30f);
+        for (int ax = 0; ax < 3; ++ax) {
+            float ext = chi[ax] - clo[ax];
+            if (!(ext > 0.f)) continue;
+            int cnt[NB] = {0};
+            float blo[NB][3], bhi[NB][3];
+            for (int b = 0; b < NB; ++b)
+                for (int k = 0; k < 3; ++k) { blo[b][k] = 1e30f; bhi[b][k] = -1e30f; }
+            for (int i = begin; i < begin + count; ++i) {
+                int b = std::min(NB - 1, (int)((tris[i].c[ax] - clo[ax]) / ext * NB));
+                cnt[b]++;
+                for (int k = 0; k < 3; ++k) {
+                    blo[b][k] = std::min(blo[b][k], tris[i].lo[k]);
+                    bhi[b][k] = std::max(bhi[b][k], tris[i].hi[k]);
+                }
+            }
+            float rlo[NB][3], rhi[NB][3];
+            int rcnt[NB];
+            float alo[3] = {1e30f, 1e30f, 1e30f}, ahi[3] = {-1e30f, -1e30f, -1e30f};
+            int acc = 0;
+            for (int b = NB - 1; b >= 0; --b) {
+                for (int k = 0; k < 3; ++k) { alo[k] = std::min(alo[k], blo[b][k]); ahi[k] = std::max(ahi[k], bhi[b][k]); }
+                acc += cnt[b];
+                std::memcpy(rlo[b], alo, sizeof(alo));
+                std::memcpy(rhi[b], ahi, sizeof(ahi));
+                rcnt[b] = acc;
+            }
+            for (int k = 0; k < 3; ++k) { alo[k] = 1e30f; ahi[k] = -1e30f; }
+            acc = 0;
+            for (int b = 0; b < NB - 1; ++b) {
+                for (int k = 0; k < 3; ++k) { alo[k] = std::min(alo[k], blo[b][k]); ahi[k] = std::max(ahi[k], bhi[b][k]); }
+                acc += cnt[b];
+                if (acc == 0 || rcnt[b + 1] == 0) continue;
+                float cost = 0.125f + (area(alo, ahi) * acc + area(rlo[b + 1], rhi[b + 1]) * rcnt[b + 1]) / parea;
+                if (cost < best_cost) { best_cost = cost; best_axis = ax; best_bin = b; }
+            }
+        }
+        int mid;
+        if (best_axis < 0) {
+            if (count <= 8) return make_leaf(begin, count);
+            mid = begin + count / 2;    // all centroids coincide: split by index
+        } else {
+            if (count <= 4 && best_cost >= (float)count) return make_leaf(begin, count);
+            float ext = chi[best_axis] - clo[best_axis];
+            auto it = std::partition(tris.begin() + begin, tris.begin() + begin + count, [&](const BTri& t) {
+                int b = std::min(NB - 1, (int)((t.c[best_axis] - clo[best_axis]) / ext * NB));
+                return b <= best_bin;
+            });
+            mid = (int)(it - tris.begin());
+            if (mid == begin || mid == begin + count) mid = begin + count / 2;
+        }
+        int me = (int)nodes.size();
+        nodes.push_back(HNode());
+        int c0 = build(begin, mid - begin, depth + 1);
+        int c1 = build(mid, begin + count - mid, depth + 1);
+        HNode& nd = nodes[me];
+        bound(&tris[begin], mid - begin, nd.lo[0], nd.hi[0]);
+        bound(&tris[mid], begin + count - mid, nd.lo[1], nd.hi[1]);
+        nd.child[0] = c0;
+        nd.child[1] = c1;
+        return me;
+    }
+};
+
+float bits_as_float(int v) {
+    float f;
+    std::memcpy(&f, &v, sizeof(f));
+    return f;
+}
+
+int upload(void** dst, const void* src, size_t bytes) {
+    if (cudaMalloc(dst, bytes == 0 ? 16 : bytes) != cudaSuccess) return VRC_ERR_OOM;
+    if (bytes && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return VRC_ERR_CUDA;
+    return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" int vrc_build_scene(const float* verts, int32_t n_verts, const int32_t* idx, int32_t n_tris,
+                               const float* albedo, const float* emission, const vrc_medium* medium,
+                               const vrc_point_light* lights, int32_t n_lights, vrc_scene** out) {
+    if (!out || !medium || n_tris < 0 || n_verts < 0 || n_lights < 0 || n_lights > VRC_MAX_LIGHTS)
+        return VRC_ERR_INVALID;
+    if (n_tris > 0 && (!verts || !idx || !albedo)) return VRC_ERR_INVALID;
+    if (n_lights > 0 && !lights) return VRC_ERR_INVALID;
+    if (n_tris >= (1 << 27)) return VRC_ERR_UNSUPPORTED;
+    *out = nullptr;
+    Builder B;
+    B.tris.resize(n_tris);
+    std::vector<float4> prim(3 * (size_t)std::max(n_tris, 1));
+    for (int t = 0; t < n_tris; ++t) {
+        double p[3][3];
+        for (int q = 0; q < 3; ++q) {
+            int vi = idx[3 * t + q];
+            if (vi < 0 || vi >= n_verts) return VRC_ERR_INVALID;
+            for (int k = 0; k < 3; ++k) p[q][k] = (double)verts[3 * vi + k];
+        }
+        BTri& bt = B.tris[t];
+        for (int k = 0; k < 3; ++k) {
+            bt.lo[k] = (float)std::min(p[0][k], std::min(p[1][k], p[2][k]));
+            bt.hi[k] = (float)std::max(p[0][k], std::max(p[1][k], p[2][k]));
+            bt.c[k] = (float)((p[0][k] + p[1][k] + p[2][k]) / 3.0);
+        }
+        bt.id = t;
+        double e1[3], e2[3], n[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = p[1][k] - p[0][k]; e2[k] = p[2][k] - p[0][k]; }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nl = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nl > 0.0)) nl = 1.0;   // zero-area triangle: never hit, normal unused
+        prim[3 * t] = make_float4((float)(n[0] / nl), (float)(n[1] / nl), (float)(n[2] / nl), 0.f);
+        prim[3 * t + 1] = make_float4(albedo[3 * t], albedo[3 * t + 1], albedo[3 * t + 2], 0.f);
+        prim[3 * t + 2] = emission ? make_float4(emission[3 * t], emission[3 * t + 1], emission[3 * t + 2], 0.f)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // root is always an inner node; a scene of <= 2 triangles gets an unreachable
+    // second child (a point box far outside the unit cube)
+    std::vector<float4> nodes;
+    std::vector<float4> tris;
+    if (n_tris > 0) {
+        B.nodes.reserve(2 * (size_t)n_tris);
+        int root = B.build(0, n_tris, 0);
+        if (B.max_depth >= VRC_STACK - 2) return VRC_ERR_UNSUPPORTED;
+        if (root < 0) {
+            HNode r;
+            Builder::bound(B.tris.data(), n_tris, r.lo[0], r.hi[0]);
+            for (int k = 0; k < 3; ++k) { r.lo[1][k] = 1e30f; r.hi[1][k] = 1e30f; }
+            r.child[0] = root;
+            r.child[1] = root;
+            B.nodes.insert(B.nodes.begin(), r);   // no inner indices to fix: the only child is a leaf
+        }
+        nodes.resize(4 * B.nodes.size());
+        for (size_t i = 0; i < B.nodes.size(); ++i) {
+            const HNode& h = B.nodes[i];
+            nodes[4 * i] = make_float4(h.lo[0][0], h.hi[0][0], h.lo[0][1], h.hi[0][1]);
+            nodes[4 * i + 1] = make_float4(h.lo[1][0], h.hi[1][0], h.lo[1][1], h.hi[1][1]);
+            nodes[4 * i + 2] = make_float4(h.lo[0][2], h.hi[0][2], h.lo[1][2], h.hi[1][2]);
+            nodes[4 * i + 3] = make_float4(bits_as_float(h.child[0]), bits_as_float(h.child[1]), 0.f, 0.f);
+        }
+        tris.resize(3 * (size_t)n_tris);
+        for (int k = 0; k < n_tris; ++k) {
+            int t = B.order[k];
+            double p[3][3];
+            for (int q = 0; q < 3; ++q)
+                for (int c = 0; c < 3; ++c) p[q][c] = (double)verts[3 * idx[3 * t + q] + c];
+            tris[3 * k] = make_float4((float)p[0][0], (float)p[0][1], (float)p[0][2], bits_as_float(t));
+            tris[3 * k + 1] = make_float4((float)(p[1][0] - p[0][0]), (float)(p[1][1] - p[0][1]),
+                                          (float)(p[1][2] - p[0][2]), 0.f);
+            tris[3 * k + 2] = make_float4((float)(p[2][0] - p[0][0]), (float)(p[2][1] - p[0][1]),
+                                          (float)(p[2][2] - p[0][2]), 0.f);
+        }
+    }
+    vrc_scene* s = (vrc_scene*)std::calloc(1, sizeof(vrc_scene));
+    if (!s) return VRC_ERR_OOM;
+    int rc = VRC_OK;
+    if ((rc = upload((void**)&s->d_nodes, nodes.data(), nodes.size() * sizeof(float4))) ||
+        (rc = upload((void**)&s->d_tris, tris.data(), tris.size() * sizeof(float4))) ||
+        (rc = upload((void**)&s->d_prim, prim.data(), prim.size() * sizeof(float4)))) {
+        vrc_destroy_scene(s);
+        return rc;
+    }
+    if (cudaMalloc((void**)&s->d_counter, 64) != cudaSuccess) {
+        vrc_destroy_scene(s);
+        return VRC_ERR_OOM;
+    }
+    s->n_prims = n_tris;
+    DevScene& d = s->dev;
+    d.nodes = s->d_nodes;
+    d.tris = s->d_tris;
+    d.prim = s->d_prim;
+    d.n_nodes = (int)(nodes.size() / 4);
+    d.n_tris = n_tris;
+    d.n_lights = n_lights;
+    for (int l = 0; l < n_lights; ++l) {
+        d.lpos[l] = make_float3(lights[l].pos[0], lights[l].pos[1], lights[l].pos[2]);
+        d.lI[l] = make_float3(lights[l].intensity[0], lights[l].intensity[1], lights[l].intensity[2]);
+    }
+    d.sigma_s = medium->sigma_s;
+    d.sigma_t = medium->sigma_s + medium->sigma_a;
+    d.g = medium->g;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    *out = s;
+    return VRC_OK;
+}
+
+extern "C" void vrc_destroy_scene(vrc_scene* s) {
+    if (!s) return;
+    cudaFree(s->d_nodes);
+    cudaFree(s->d_tris);
+    cudaFree(s->d_prim);
+    cudaFree(s->d_counter);
+    cudaFree(s->h_stage_dev);
+    std::free(s);
+}
+
+extern "C" const char* vrc_status_string(int st) {
+    switch (st) {
+        case VRC_OK: return "ok";
+        case VRC_ERR_INVALID: return "invalid argument";
+        case VRC_ERR_OOM: return "out of memory";
+        case VRC_ERR_CUDA: return "CUDA error";
+        case VRC_ERR_TIMEOUT: return "device wait timed out";
+        case VRC_ERR_UNSUPPORTED: return "unsupported size";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int vrc_version(void) { return 100; }

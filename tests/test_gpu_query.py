@@ -1,0 +1,115 @@
+"""GPU parity of the record grid and query kernel (Eq. radianceTaylor) against the oracle.
+
+The query path is checked on seeded synthetic record tables (so the records are
+inputs common to both sides), then end to end: GPU records -> GPU queries against
+oracle records -> oracle queries.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_helpers import to_np
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vrc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_09258_gb300 import build
+    build.build()
+    import paper_1805_09258_gb300 as m
+    return m
+
+
+def synthetic_table(n, seed, r_lo=0.03, r_hi=0.3):
+    rng = np.random.default_rng(seed)
+    tab = dict(pos=rng.uniform(0.0, 1.0, size=(n, 3)), radius=rng.uniform(r_lo, r_hi, size=n),
+               L=rng.uniform(0.05, 1.0, size=(n, 3)), grad=rng.normal(size=(n, 9)) * 0.5,
+               hess=rng.normal(size=(n, 18)) * 2.0)
+    return {k: v.astype(np.float32) for k, v in tab.items()}
+
+
+def gpu_query(vrc, tab, q, order):
+    recs = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in tab.items()}
+    grid = vrc.Grid(recs, extrap_order=order)
+    rgb, cnt = vrc.query_inscatter(grid, torch.from_numpy(np.ascontiguousarray(q)).cuda())
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), cnt.cpu().numpy(), grid
+
+
+def check_query(rgb, cnt, ref, rc, near):
+    ok = near == 0
+    assert np.array_equal(cnt[ok], rc[ok])                      # membership is integer work: exact
+    assert np.all(np.abs(cnt[~ok] - rc[~ok]) <= 2)
+    hit = ok & (rc > 0)
+    scale = np.abs(ref[hit]).max(axis=1, keepdims=True) + np.abs(ref[hit]) + 1e-6
+    assert np.all(np.abs(rgb[hit] - ref[hit]) <= 2e-5 * scale + 1e-6)
+    assert np.all(rgb[rc == 0] == 0)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_synthetic_table_parity(vrc, order):
+    tab = synthetic_table(500, seed=21)
+    rng = np.random.default_rng(22)
+    q = np.concatenate([rng.uniform(0, 1, size=(20000, 3)), tab["pos"][:50],        # record centres
+                        rng.uniform(0.98, 1.0, size=(100, 3))]).astype(np.float32)  # cube corner
+    rgb, cnt, _ = gpu_query(vrc, tab, q, order)
+    ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=order)
+    check_query(rgb, cnt, ref, rc, near)
+    assert np.allclose(rgb[20000:20050], tab["L"][:50] * 0 + rgb[20000:20050])   # finite at centres
+    assert cnt.max() > 1 and (cnt == 0).any()
+
+
+def test_sizes_ragged_and_degenerate(vrc):
+    rng = np.random.default_rng(23)
+    for n, nq in ((1, 7), (3, 1), (33, 1000), (2049, 4097)):
+        tab = synthetic_table(n, seed=n)
+        q = rng.uniform(0, 1, size=(nq, 3)).astype(np.float32)
+        rgb, cnt, _ = gpu_query(vrc, tab, q, 1)
+        ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], None, q, order=1)
+        check_query(rgb, cnt, ref, rc, near)
+    # tiny radii: most queries miss; huge radii: every record covers every query
+    for r_lo, r_hi in ((1e-3, 2e-3), (1.9, 2.0)):
+        tab = synthetic_table(200, seed=7, r_lo=r_lo, r_hi=r_hi)
+        q = rng.uniform(0, 1, size=(3000, 3)).astype(np.float32)
+        rgb, cnt, _ = gpu_query(vrc, tab, q, 1)
+        ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], None, q, order=1)
+        check_query(rgb, cnt, ref, rc, near)
+
+
+def test_zero_queries_and_empty_table(vrc):
+    tab = synthetic_table(10, seed=1)
+    q0 = np.zeros((0, 3), np.float32)
+    rgb, cnt, grid = gpu_query(vrc, tab, q0, 1)
+    assert rgb.shape == (0, 3)
+    empty = {k: v[:0] for k, v in tab.items()}
+    rgb, cnt, _ = gpu_query(vrc, empty, np.random.default_rng(0).uniform(0, 1, (50, 3)).astype(np.float32), 1)
+    assert np.all(cnt == 0) and np.all(rgb == 0)
+
+
+def test_records_then_queries_end_to_end(vrc):
+    """Small workload: GPU records + GPU queries vs oracle records + oracle queries."""
+    w = W.config1()
+    pos = w.positions()
+    q = w.queries()
+    s = vrc.Scene.from_workload(w.scene)
+    out = vrc.compute_records(s, torch.from_numpy(pos).cuda(), w.params)
+    grid = vrc.Grid(out)
+    rgb, cnt = vrc.query_inscatter(grid, torch.from_numpy(q).cuda())
+    torch.cuda.synchronize()
+    rgb, cnt = rgb.cpu().numpy(), cnt.cpu().numpy()
+    ref = O.records(O.OracleScene(w.scene), w.params, pos, track_margins=1)
+    qo, qc, near = O.query(pos, ref["radius"], ref["L"], ref["grad"], ref["hess"], q, order=1)
+    # radii agree to ~1e-4, so membership may differ only for queries near a boundary
+    g = to_np(out)
+    rel_r = np.abs(g["radius"] - ref["radius"]) / ref["radius"]
+    d = np.linalg.norm(q[:, None, :].astype(np.float64) - pos[None].astype(np.float64), axis=2)
+    margin = np.abs(d - ref["radius"][None]) / ref["radius"][None]
+    sensitive = (margin < 5 * rel_r.max() + 1e-5).any(axis=1)
+    assert np.array_equal(cnt[~sensitive], qc[~sensitive])
+    both = (~sensitive) & (qc > 0)
+    assert np.all(np.abs(rgb[both] - qo[both]) <= 2e-3 * np.abs(qo[both]).max(axis=1, keepdims=True) + 1e-6)

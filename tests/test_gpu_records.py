@@ -1,0 +1,154 @@
+"""GPU parity of cache records (through the C ABI) against the FP64 oracle.
+
+Workloads: the small one in full (64 records x 16x32 rays); the mid one at its full
+size in the benchmark's launch configuration (4,096 records x 32x64 rays) with a
+seeded sample of records recomputed by the oracle; ragged and chunked launches
+(odd band/bin counts, several shared-memory chunks, per-record band counts); and the
+edge cases (no records, an empty scene, the smallest ray sets, |A| form factors,
+invalid arguments).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_helpers import compare_radius, compare_records, to_np
+from workloads.configs import RecordParams
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vrc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_09258_gb300 import build
+    build.build()
+    import paper_1805_09258_gb300 as m
+    return m
+
+
+def run_gpu(vrc, scene, params, pos, n_bands=None, debug_hits=False, tuning=None):
+    s = vrc.Scene.from_workload(scene)
+    if tuning:
+        s.set_tuning(**tuning)
+    nbt = None if n_bands is None else torch.from_numpy(np.asarray(n_bands, np.int32)).cuda()
+    out = vrc.compute_records(s, torch.from_numpy(np.ascontiguousarray(pos)).cuda(), params, n_bands=nbt,
+                              debug_hits=debug_hits)
+    torch.cuda.synchronize()
+    return to_np(out)
+
+
+def test_small_workload_all_records(vrc):
+    w = W.config1()
+    pos = w.positions()
+    g = run_gpu(vrc, w.scene, w.params, pos)
+    ref = O.records(O.OracleScene(w.scene), w.params, pos, track_margins=1)
+    st = compare_records(g, ref)
+    compare_radius(g, ref)
+    assert st["zero_budget"] >= 0.8 * st["n"]
+    assert np.allclose(g["pos"], pos)
+
+
+def test_mid_workload_full_size_sampled(vrc):
+    """All 4,096 records of the mid workload in one launch; 24 seeded samples re-done by the oracle."""
+    w = W.config2()
+    pos = w.positions()
+    g = run_gpu(vrc, w.scene, w.params, pos)
+    idx = np.sort(np.random.default_rng(99).choice(pos.shape[0], 24, replace=False))
+    ref = O.records(O.OracleScene(w.scene), w.params, pos[idx], rec_ids=idx, track_margins=1)
+    compare_records(g, ref, idx)
+    compare_radius(g, ref, idx)
+    assert np.all(np.isfinite(g["L"])) and np.all(np.isfinite(g["hess"]))
+
+
+def test_ragged_sizes_and_chunks(vrc):
+    """Odd band and bin counts, a ragged record count, and ray sets split into many chunks."""
+    w = W.config2()
+    rp = RecordParams(n_bands=13, n_bins=27)
+    pos = w.positions(37, seed=77)
+    ref = O.records(O.OracleScene(w.scene), rp, pos, track_margins=1)
+    for tuning in (None, dict(threads=128, chunk_bands=3), dict(threads=512, chunk_bands=5)):
+        g = run_gpu(vrc, w.scene, rp, pos, tuning=tuning)
+        compare_records(g, ref)
+        compare_radius(g, ref)
+
+
+def test_per_record_band_counts(vrc):
+    """Uneven ray sets in one launch: record i uses n_bands[i] bands and 2 n_bands[i] bins."""
+    w = W.config2()
+    pos = w.positions(40, seed=78)
+    nb = np.random.default_rng(5).integers(2, 14, size=40).astype(np.int32)
+    rp = RecordParams(n_bands=int(nb.max()), n_bins=2 * int(nb.max()))
+    g = run_gpu(vrc, w.scene, rp, pos, n_bands=nb)
+    ref = O.records(O.OracleScene(w.scene), rp, pos, n_bands=nb, track_margins=1)
+    compare_records(g, ref)
+
+
+def test_smallest_ray_sets_and_abs_formfactor(vrc):
+    w = W.config1()
+    pos = w.positions(16)
+    for nb, ns, signed in ((1, 3, 1), (2, 4, 1), (3, 5, 0), (8, 16, 0)):
+        rp = RecordParams(n_bands=nb, n_bins=ns, ff_signed=signed)
+        g = run_gpu(vrc, w.scene, rp, pos)
+        ref = O.records(O.OracleScene(w.scene), rp, pos, track_margins=1)
+        compare_records(g, ref)
+
+
+def test_empty_scene_and_anisotropic_phase(vrc):
+    """No triangles: every ray leaves the cube; strongly forward-scattering medium."""
+    from workloads.scenes import Medium, PointLight, Scene
+    sc = Scene(tris=np.zeros((0, 3, 3), np.float32), albedo=np.zeros((0, 3), np.float32),
+               medium=Medium(0.6, 0.1, 0.8), lights=[PointLight((0.3, 0.6, 0.7), (2.0, 1.0, 0.5))])
+    rp = RecordParams(n_bands=16, n_bins=32, omega_o=(0.6, 0.0, 0.8))
+    pos = np.random.default_rng(3).uniform(0.05, 0.95, size=(20, 3)).astype(np.float32)
+    g = run_gpu(vrc, sc, rp, pos)
+    ref = O.records(O.OracleScene(sc), rp, pos, track_margins=1)
+    compare_records(g, ref)
+    assert np.all(g["L_ss"] == 0)
+
+
+def test_zero_records_and_invalid_arguments(vrc):
+    w = W.config1()
+    s = vrc.Scene.from_workload(w.scene)
+    empty = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    out = vrc.compute_records(s, empty, w.params)
+    assert out["L"].shape == (0, 3)
+    bad = RecordParams(n_bands=300, n_bins=32)
+    with pytest.raises(vrc.VrcError, match="unsupported"):
+        vrc.compute_records(s, torch.zeros((2, 3), dtype=torch.float32, device="cuda"), bad)
+    with pytest.raises(vrc.VrcError, match="invalid"):
+        vrc.compute_records(s, torch.zeros((2, 3), dtype=torch.float32, device="cuda"),
+                            RecordParams(n_bands=4, n_bins=2))
+
+
+def test_host_buffer_entry_point_matches_device_entry_point(vrc):
+    w = W.config1()
+    pos = w.positions(32)
+    s = vrc.Scene.from_workload(w.scene)
+    d = to_np(vrc.compute_records(s, torch.from_numpy(pos).cuda(), w.params))
+    h = vrc.compute_records_host(s, pos, w.params)
+    for k in ("L", "grad", "hess", "radius", "status"):
+        assert np.array_equal(h[k], d[k]), k
+
+
+def test_hit_ids_agree_except_near_edges(vrc):
+    """Primary hit primitive ids agree on >= 99.99% of rays; a mismatch is allowed only
+    where the oracle's ray passes within 1e-5 of a triangle edge (or meets two
+    coplanar triangles at the same t)."""
+    total = mism = 0
+    for w, n in ((W.config1(), 64), (W.config2(), 16)):
+        pos = w.positions(n)
+        g = run_gpu(vrc, w.scene, w.params, pos, debug_hits=True)
+        ref = O.records(O.OracleScene(w.scene), w.params, pos, track_margins=1, debug=True)
+        V = w.params.n_rays
+        gh, oh = g["hit_prim"][:, :V], ref["hit_prim"][:, :V]
+        bad = gh != oh
+        total += gh.size
+        mism += int(bad.sum())
+        ok_tie = (ref["hit_margin"][:, :V] < 1e-5) | (ref["hit_tie"][:, :V] < 1e-5)
+        assert np.all(ok_tie[bad]), np.argwhere(bad & ~ok_tie)[:5]
+        same = ~bad
+        assert np.allclose(g["hit_t"][:, :V][same], ref["hit_t"][:, :V][same], rtol=2e-5, atol=1e-6)
+    assert mism <= 1e-4 * total + 1
