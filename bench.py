@@ -152,7 +152,7 @@ def run_reference(args, w, rank, world):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    n_rec, n_q = 192, 16384
+    n_rec, n_q = 256, 16384
     # warm-up steps (untimed) then K timed steps of the bounded sample
     for _ in range(max(0, min(args.warmup, 1))):
         oracle_rates(w, 16, 1024, threads)
@@ -254,6 +254,18 @@ def run_gpu(args, w, rank, world, local_rank):
     st = rec["status"].cpu().numpy()
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
+    if args.no_e2e:
+        e2e_s, h2d, d2h = float("nan"), 0, 0
+    else:
+        e2e_s, h2d, d2h = e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, flush)
+    line = None
+    if rank == 0:
+        line = report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h)
+    return line
+
+
+def e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, flush):
+    import torch
     h_pos = torch.from_numpy(pos_np).pin_memory()
     h_q = torch.from_numpy(q_np).pin_memory()
     h_rgb = torch.empty((w.n_queries, 3), dtype=torch.float32).pin_memory()
@@ -287,9 +299,12 @@ def run_gpu(args, w, rank, world, local_rank):
     e2e_s = float(np.mean(e2e_t))
     h2d = h_pos.numel() * 4 + h_q.numel() * 4
     d2h = sum(v.numel() * 4 for v in h_out.values()) + h_rgb.numel() * 4 + h_cnt.numel() * 4
+    return e2e_s, h2d, d2h
 
-    line = None
-    if rank == 0:
+
+def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h):
+    value = world * w.n_records / (ms * 1e-3)
+    if True:
         clk = clocks.summary()
         peaks = measured_peaks()
         fp32_peak = fp32_peak_tflops(2070.0)
@@ -312,8 +327,10 @@ def run_gpu(args, w, rank, world, local_rank):
                              "lit_cells_per_launch": int(n_cells.sum()), "far_vertex_evals": int(n_far.sum()),
                              "flop_per_launch": flop},
                 "clocks": clk,
-                "e2e": {"value": world * w.n_records / e2e_s, "unit": "records/s", "h2d_bytes_per_step": int(h2d),
-                        "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
+                "e2e": None if math.isnan(e2e_s) else
+                {"value": world * w.n_records / e2e_s, "unit": "records/s", "h2d_bytes_per_step": int(h2d),
+                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+                 "path": "pinned host -> compute_records -> build_record_grid -> query_inscatter -> pinned host"},
                 "gpu_launches": None,
                 "record_status": {"ok": int((st == 0).sum()), "clamped": int(((st & 6) != 0).sum()),
                                   "nonfinite": int(((st & 1) != 0).sum())},
@@ -323,12 +340,14 @@ def run_gpu(args, w, rank, world, local_rank):
         # scatter + query = 6
         line["gpu_launches"] = args.steps * (1 + 7 + 6)
         if not args.no_cpu_baseline:
-            rr, qr, spent = oracle_rates(w, 96, 8192, os.cpu_count() or 1)
+            n_rec, n_q = w.n_records, min(w.n_queries, 131072)
+            rr, qr, spent = oracle_rates(w, n_rec, n_q, os.cpu_count() or 1)
             t_cpu = w.n_records / rr + w.n_queries / qr
             line["cpu_baseline"] = {"value": w.n_records / t_cpu, "unit": "records/s", "cores": os.cpu_count(),
                                     "kind": "oracle", "cpu": cpu_model(),
-                                    "sample": "96 of the 4,096 records (all host threads) and 8,192 of the 1M "
-                                              "queries (brute force, 1 thread); full-step time extrapolated",
+                                    "sample": f"all {n_rec} records (one per host thread at a time) and {n_q} of the "
+                                              f"{w.n_queries} queries (brute force over all records, 1 thread); "
+                                              "query time scaled to the full batch",
                                     "records_per_s": rr, "queries_per_s": qr, "seconds": spent}
         print(json.dumps(line), flush=True)
     return line
@@ -337,15 +356,22 @@ def run_gpu(args, w, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
+    ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     w = W.config2()
+    if args.records:
+        w.n_records = args.records
+    if args.queries:
+        w.n_queries = args.queries
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return

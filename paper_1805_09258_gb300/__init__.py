@@ -275,3 +275,4 @@ def query_inscatter(grid: Grid, q, rgb=None, status=None, stream=None):
     rc = load_library().vrc_query_inscatter(grid.handle, _ptr(q), nq, _ptr(rgb), _ptr(status), _stream_ptr(stream))
     _check(rc, "vrc_query_inscatter")
     return rgb, status
+
