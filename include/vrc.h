@@ -181,6 +181,34 @@ void vrc_destroy_grid(vrc_grid* grid);
 int vrc_query_inscatter(const vrc_grid* grid, const float* d_q, int32_t nq, float* d_rgb, int32_t* d_status,
                         void* stream);
 
+/* Queries for callers that cannot allocate device memory.
+ *
+ * No counterpart in the paper: this is a library convenience.  vrc_query_inscatter
+ * needs a vrc_grid, which vrc_build_record_grid allocates; some callers cannot call
+ * cudaMalloc at query time -- a host application or plugin framework that owns all
+ * device memory and hands out fixed pools, a real-time renderer that forbids
+ * allocation after start-up because cudaMalloc may synchronise the device and stall
+ * its other streams, a service with a hard pre-reserved memory budget.  This entry
+ * point answers the same queries (same Eq. radianceTaylor, same results within float
+ * rounding) straight from the caller's record buffers and allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine.  Its working memory is one
+ * file-scope device array of VRC_NOALLOC_SCRATCH_INTS 32-bit words (4 MiB) that every
+ * GPU loading the library holds until the process exits.
+ *   recs     device records: pos, radius, L, grad (and hess for extrap_order 2)
+ *   n        number of records, at most VRC_NOALLOC_MAX_RECORDS (else VRC_ERR_UNSUPPORTED)
+ *   d_q, nq, d_rgb, d_status   as for vrc_query_inscatter
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every
+ * call reuses the same array and leaves its contents behind, so two calls that overlap
+ * on the GPU (different streams without ordering, or concurrent host threads) race and
+ * may return wrong results: order them on one stream.  If the record lists do not fit
+ * in the array the queries scan every record instead (same answer, slower).
+ * Asynchronous on `stream`. */
+#define VRC_NOALLOC_SCRATCH_INTS (1 << 20)
+#define VRC_NOALLOC_MAX_RECORDS 65536
+int vrc_query_inscatter_noalloc(const vrc_records_view* recs, int32_t n, int32_t extrap_order, const float* d_q,
+                                int32_t nq, float* d_rgb, int32_t* d_status, void* stream);
+
 /* --------------------------------------------------------------- misc */
 const char* vrc_status_string(int status);
 int vrc_version(void);

@@ -76,6 +76,7 @@ def load_library(path: Optional[str] = None):
     L.vrc_destroy_grid.argtypes = [P]
     L.vrc_destroy_grid.restype = None
     L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
+    L.vrc_query_inscatter_noalloc.argtypes = [P, I32, I32, P, I32, P, P, P]
     L.vrc_status_string.restype = C.c_char_p
     L.vrc_status_string.argtypes = [C.c_int]
     _lib = L
@@ -276,3 +277,29 @@ def query_inscatter(grid: Grid, q, rgb=None, status=None, stream=None):
     _check(rc, "vrc_query_inscatter")
     return rgb, status
 
+
+NOALLOC_MAX_RECORDS = 65536
+
+
+def query_inscatter_noalloc(records: dict, q, n: Optional[int] = None, extrap_order: int = 1, rgb=None,
+                            status=None, stream=None):
+    """vrc_query_inscatter_noalloc: the same queries without a grid object.
+
+    For callers that cannot allocate device memory at query time: the library uses a
+    fixed 4 MiB device array instead of cudaMalloc.  Calls that overlap on the GPU race
+    on that array; keep them ordered on one stream.  The first call on a device should
+    come before any stream capture.
+    """
+    torch = _torch()
+    assert q.is_cuda and q.dtype == torch.float32 and q.is_contiguous()
+    n = records["L"].shape[0] if n is None else n
+    nq = q.shape[0]
+    if rgb is None:
+        rgb = torch.empty((nq, 3), dtype=torch.float32, device=q.device)
+    if status is None:
+        status = torch.empty((nq,), dtype=torch.int32, device=q.device)
+    v = records_view(records)
+    rc = load_library().vrc_query_inscatter_noalloc(C.byref(v), n, extrap_order, _ptr(q), nq, _ptr(rgb),
+                                                    _ptr(status), _stream_ptr(stream))
+    _check(rc, "vrc_query_inscatter_noalloc")
+    return rgb, status
