@@ -139,6 +139,7 @@ typedef struct {
     int32_t threads;        /* threads per block: 128, 256, 512 */
     int32_t chunk_bands;    /* bands of the ray set kept in shared memory at once */
     int32_t blocks_per_sm;  /* persistent blocks per SM */
+    int32_t shadow_bvh;     /* 1: shadow rays traverse the BVH; 0: light buffer (default) */
 } vrc_record_tuning;
 
 /* Compute n records at d_pos [n][3] (Secs. 4-5 and App. A, C): trace the stratified

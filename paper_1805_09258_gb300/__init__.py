@@ -49,7 +49,8 @@ class RecordsView(C.Structure):
 
 
 class RecordTuning(C.Structure):
-    _fields_ = [("threads", C.c_int32), ("chunk_bands", C.c_int32), ("blocks_per_sm", C.c_int32)]
+    _fields_ = [("threads", C.c_int32), ("chunk_bands", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("shadow_bvh", C.c_int32)]
 
 
 _lib = None
@@ -147,14 +148,15 @@ class Scene:
     def from_workload(cls, scene):
         return cls(scene.tris, scene.albedo, scene.medium, scene.lights, scene.emission)
 
-    def set_tuning(self, threads=0, chunk_bands=0, blocks_per_sm=0):
-        t = RecordTuning(threads, chunk_bands, blocks_per_sm)
+    def set_tuning(self, threads=0, chunk_bands=0, blocks_per_sm=0, shadow_bvh=0):
+        t = RecordTuning(threads, chunk_bands, blocks_per_sm, shadow_bvh)
         _check(load_library().vrc_set_record_tuning(self.handle, C.byref(t)), "vrc_set_record_tuning")
 
     def get_tuning(self):
         t = RecordTuning()
         _check(load_library().vrc_get_record_tuning(self.handle, C.byref(t)), "vrc_get_record_tuning")
-        return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm)
+        return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm,
+                    shadow_bvh=t.shadow_bvh)
 
     def __del__(self):
         try:

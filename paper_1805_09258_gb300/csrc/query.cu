@@ -84,15 +84,32 @@ __global__ void k_insert(const float4* rec, int n, int G, int* counts, const int
             }
 }
 
-// sort each cell's list ascending (deterministic summation order in the queries)
-__global__ void k_sort_lists(const int* start, int ncell, int* list) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+// Sort each cell's list ascending (a deterministic summation order for the queries).
+// One block per cell: record ids in a list are distinct, so each element's position is
+// the number of smaller elements (rank sort in shared memory); lists longer than the
+// shared buffer fall back to an insertion sort by one thread.
+constexpr int SORT_CAP = 4096;
+__global__ void __launch_bounds__(256) k_sort_lists(const int* start, int ncell, int* list) {
+    __shared__ int buf[SORT_CAP];
+    int cell = blockIdx.x;
     if (cell >= ncell) return;
-    int b = start[cell], e = start[cell + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = list[i], j = i - 1;
-        while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
-        list[j + 1] = v;
+    int b = start[cell], e = start[cell + 1], len = e - b;
+    if (len <= 1) return;
+    if (len > SORT_CAP) {
+        if (threadIdx.x == 0)
+            for (int i = b + 1; i < e; ++i) {
+                int v = list[i], j = i - 1;
+                while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
+                list[j + 1] = v;
+            }
+        return;
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = list[b + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        int v = buf[i], r = 0;
+        for (int j = 0; j < len; ++j) r += buf[j] < v;
+        list[b + r] = v;
     }
 }
 
@@ -294,7 +311,7 @@ extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32
         }
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
         k_insert<true><<<nbk, tb, 0, st>>>(g->rec, n, G, g->q_count, g->cell_start, g->cell_list);
-        k_sort_lists<<<(ncell + 127) / 128, 128, 0, st>>>(g->cell_start, ncell, g->cell_list);
+        k_sort_lists<<<ncell, 256, 0, st>>>(g->cell_start, ncell, g->cell_list);
     } else {
         cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);
         if ((rc = dev_alloc(&g->cell_list, 1))) {

@@ -71,8 +71,7 @@ __device__ float3 medium_radiance(const DevScene& sc, float3 y, float3 d) {
         float d2 = dot3(lv, lv);
         float dist = sqrtf(d2);
         float3 lh = lv * (1.0f / dist);
-        float th;
-        if (bvh_trace<true>(sc, y, lh, VRC_TMIN, dist, &th) >= 0) continue;
+        if (shadow_occluded(sc, l, y, lh, dist)) continue;
         float f = hg_dev(dot3(lh, d), sc.g);      // light p_L -> y, then y -> x along -d
         float w = f * __expf(-sc.sigma_t * dist) / d2;
         L = L + sc.lI[l] * w;
@@ -98,8 +97,7 @@ __device__ float3 surface_radiance(const DevScene& sc, int prim, float3 y, float
         float3 o = y + n * 1e-5f;
         float3 lo = sc.lpos[l] - o;
         float dl = sqrtf(dot3(lo, lo));
-        float th;
-        if (bvh_trace<true>(sc, o, lo * (1.0f / dl), VRC_TMIN, dl, &th) >= 0) continue;
+        if (shadow_occluded(sc, l, o, lo * (1.0f / dl), dl)) continue;
         float w = cs * __expf(-sc.sigma_t * dist) / (d2 * VRC_PI_F);
         L = L + f3(al.x * sc.lI[l].x, al.y * sc.lI[l].y, al.z * sc.lI[l].z) * w;
     }
@@ -296,13 +294,14 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ float4 smem4[];
     float4* ray = smem4;                                     // (d, t_end) per chunk vertex
-    float* Lr = reinterpret_cast<float*>(ray + a.cap);
+    float* Lr = reinterpret_cast<float*>(ray + a.cap);       // [2][3][cap] vertex radiance, double-buffered
     float* Lg = Lr + a.cap;
     float* Lb = Lg + a.cap;
-    float* red = Lb + a.cap;                                 // [NW][32][4]
+    float* red = Lr + 6 * a.cap;                             // [NW][32][4]
     float* mcs = red + NW * 32 * 4;                          // [NW][12]
     float* tot = mcs + NW * 12;                              // [128]
     int* misc = reinterpret_cast<int*>(tot + 128);           // [4]
+    int* wq = misc + 4;                                      // [NW][64] lit-cell queues
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float sigma_t = sc.sigma_t, g = sc.g;
     __shared__ int s_rec;
@@ -380,57 +379,65 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
             // cells of this chunk
             const int nq = r1e - r0;                         // quad bands with upper row in [r0, r1e)
             const int ncell = (north ? ns : 0) + 2 * ns * nq + (south ? ns : 0);
+            // Shell k's cell phase reads radiance buffer k & 1 while the same phase computes
+            // shell k + 1's vertex radiance into the other buffer: one barrier per shell, and
+            // the shadow-ray latency of some warps overlaps the cell arithmetic of others.
             for (int k = 0; k <= K; ++k) {
                 const float tk = ((float)k - 0.5f) * a.dt;
-                if (k > 0) {
-                    // ---------------- vertex phase of medium shell k
+                const float* Lrk = Lr + (k & 1) * (3 * a.cap);
+                const float* Lgk = Lrk + a.cap;
+                const float* Lbk = Lgk + a.cap;
+                if (k + 1 <= K) {
+                    // ---------------- vertex phase of medium shell k + 1
+                    const float tn = ((float)(k + 1) - 0.5f) * a.dt;
+                    float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
                     for (int lv = tid; lv < nvert; lv += NT) {
                         float4 rv = ray[lv];
                         float3 d = f3(rv.x, rv.y, rv.z);
                         float3 Lo = f3(0.f, 0.f, 0.f);
-                        if (tk < rv.w) {
-                            Lo = medium_radiance(sc, x + d * tk, d);
+                        if (tn < rv.w) {
+                            Lo = medium_radiance(sc, x + d * tn, d);
                             bool pole = lv >= rows * ns;
                             bool owned = !pole && (r0 + lv / ns) < r1;
                             if (owned) {
-                                float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * tk);
+                                float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * tn);
                                 neumaier(mc[3], mcc[3], w * Lo.x);
                                 neumaier(mc[4], mcc[4], w * Lo.y);
                                 neumaier(mc[5], mcc[5], w * Lo.z);
                             }
                         }
-                        Lr[lv] = Lo.x;
-                        Lg[lv] = Lo.y;
-                        Lb[lv] = Lo.z;
+                        Lrn[lv] = Lo.x;
+                        Lrn[a.cap + lv] = Lo.y;
+                        Lrn[2 * a.cap + lv] = Lo.z;
                     }
-                    __syncthreads();
                 }
-                // ---------------- cell phase of shell k
-                const int nround = (ncell + 31) & ~31;
-                for (int base = warp * 32; base < nround; base += NT) {
+                // ---------------- cell phase of shell k: lit cells are compacted into a
+                // per-warp queue so cell_eval runs with all 32 lanes busy
+                auto cell_verts = [&](int cc, int (&vi)[3]) {
+                    if (north && cc < ns) {
+                        vi[0] = PN; vi[1] = cc; vi[2] = (cc + 1) % ns;
+                        return;
+                    }
+                    if (north) cc -= ns;
+                    if (cc < 2 * ns * nq) {
+                        int qd = cc >> 1, ri = qd / ns, j = qd - ri * ns, j1 = (j + 1) % ns;
+                        int v00 = ri * ns + j, v01 = ri * ns + j1, v10 = (ri + 1) * ns + j, v11 = (ri + 1) * ns + j1;
+                        if ((cc & 1) == 0) { vi[0] = v00; vi[1] = v10; vi[2] = v11; }
+                        else { vi[0] = v00; vi[1] = v11; vi[2] = v01; }
+                        return;
+                    }
+                    cc -= 2 * ns * nq;
+                    int rl = (nb - 1 - r0) * ns;
+                    vi[0] = PS; vi[1] = rl + (cc + 1) % ns; vi[2] = rl + cc;
+                };
+                auto process = [&](int c) {
                     float v[32];
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = 0.f;
-                    int c = base + lane;
                     int m = 0;
-                    if (c < ncell) {
+                    if (c >= 0) {
                         int vi[3];
-                        int cc = c;
-                        if (north && cc < ns) {
-                            vi[0] = PN; vi[1] = cc; vi[2] = (cc + 1) % ns;
-                        } else {
-                            if (north) cc -= ns;
-                            if (cc < 2 * ns * nq) {
-                                int qd = cc >> 1, ri = qd / ns, j = qd - ri * ns, j1 = (j + 1) % ns;
-                                int v00 = ri * ns + j, v01 = ri * ns + j1, v10 = (ri + 1) * ns + j, v11 = (ri + 1) * ns + j1;
-                                if ((cc & 1) == 0) { vi[0] = v00; vi[1] = v10; vi[2] = v11; }
-                                else { vi[0] = v00; vi[1] = v11; vi[2] = v01; }
-                            } else {
-                                cc -= 2 * ns * nq;
-                                int rl = (nb - 1 - r0) * ns;
-                                vi[0] = PS; vi[1] = rl + (cc + 1) % ns; vi[2] = rl + cc;
-                            }
-                        }
+                        cell_verts(c, vi);
                         float3 rr[3], Lo[3];
                         float tt[3];
 #pragma unroll
@@ -439,7 +446,7 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                             float tq = (k == 0 || !(tk < rv.w)) ? rv.w : tk;
                             tt[q] = tq;
                             rr[q] = f3(rv.x * tq, rv.y * tq, rv.z * tq);
-                            Lo[q] = f3(Lr[vi[q]], Lg[vi[q]], Lb[vi[q]]);
+                            Lo[q] = f3(Lrk[vi[q]], Lgk[vi[q]], Lbk[vi[q]]);
                         }
                         m = cell_eval(rr, tt, Lo, sigma_t, g, a.wo, a.ff_signed, v);
                     }
@@ -453,6 +460,44 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                     float mine = warp_transpose_reduce(v, lane);
                     if (k == 0) neumaier(acc_s, cmp_s, mine);
                     else neumaier(acc_m, cmp_m, mine);
+                };
+                int* wqw = wq + warp * 64;
+                int qn = 0;
+                const int nround = (ncell + 31) & ~31;
+                for (int base = warp * 32; base < nround; base += NT) {
+                    int c = base + lane;
+                    bool lit = false;
+                    if (c < ncell) {
+                        // a cell contributes iff one of its furthest vertices has radiance
+                        int vi[3];
+                        cell_verts(c, vi);
+                        float tq[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            float te = ray[vi[q]].w;
+                            tq[q] = (k == 0 || !(tk < te)) ? te : tk;
+                        }
+                        float tmx = fmaxf(tq[0], fmaxf(tq[1], tq[2]));
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            if (tq[q] == tmx && (Lrk[vi[q]] != 0.f || Lgk[vi[q]] != 0.f || Lbk[vi[q]] != 0.f))
+                                lit = true;
+                    }
+                    unsigned msk = __ballot_sync(0xffffffffu, lit);
+                    if (lit) wqw[qn + __popc(msk & ((1u << lane) - 1u))] = c;
+                    qn += __popc(msk);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        process(wqw[lane]);
+                        __syncwarp();
+                        if (lane < qn - 32) wqw[lane] = wqw[lane + 32];
+                        __syncwarp();
+                        qn -= 32;
+                    }
+                }
+                if (qn > 0) {
+                    process(lane < qn ? wqw[lane] : -1);
+                    __syncwarp();
                 }
                 __syncthreads();
             }
@@ -567,7 +612,8 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
 
 size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
-    return (size_t)cap * 16 + (size_t)cap * 12 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4;
+    return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
+           (size_t)nw * 64 * 4;
 }
 
 template <int NT>
@@ -582,7 +628,9 @@ int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st)
     int grid = per_sm * s->sm_count;
     if (grid > a.n) grid = a.n;
     if (grid < 1) grid = 1;
-    kfn<<<grid, NT, smem, st>>>(s->dev, a);
+    DevScene dv = s->dev;
+    dv.use_lb = s->tuning.shadow_bvh ? 0 : 1;
+    kfn<<<grid, NT, smem, st>>>(dv, a);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
@@ -591,7 +639,7 @@ int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st)
 extern "C" int vrc_set_record_tuning(vrc_scene* s, const vrc_record_tuning* t) {
     if (!s || !t) return VRC_ERR_INVALID;
     if (t->threads != 0 && t->threads != 128 && t->threads != 256 && t->threads != 512) return VRC_ERR_INVALID;
-    if (t->chunk_bands < 0 || t->blocks_per_sm < 0) return VRC_ERR_INVALID;
+    if (t->chunk_bands < 0 || t->blocks_per_sm < 0 || t->shadow_bvh < 0 || t->shadow_bvh > 1) return VRC_ERR_INVALID;
     s->tuning = *t;
     return VRC_OK;
 }

@@ -4,6 +4,7 @@
 // in HBM as a two-wide BVH built on the host with binned surface-area heuristic
 // splits, traversed by the library's own kernels (vrc_internal.cuh).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -133,6 +134,100 @@ float bits_as_float(int v) {
     return f;
 }
 
+// ---------------------------------------------------------------- light buffer
+// For each cube face around the light (face = 2 axis + (negative ? 1 : 0); coordinates
+// m along the axis, a and b the next two axes cyclically) the triangle is clipped to the
+// face's frustum m >= |a|, m >= |b| (Sutherland-Hodgman), projected to (a/m, b/m), and its
+// padded bounding rectangle of cells receives the triangle.  The gnomonic projection maps
+// the clipped polygon onto a convex polygon inside that rectangle, so every direction the
+// triangle covers (and a margin for rounding and for the widened triangle test) lands in
+// a cell that lists it.  Entries of a cell are sorted by a lower bound of the triangle's
+// distance to the light (distance from the light to the triangle's bounding box).
+struct LightBufHost {
+    std::vector<int> start;
+    std::vector<int2> ent;
+};
+
+void build_light_buffer(const std::vector<std::array<double, 9>>& tv, const std::vector<int>& bvh_index,
+                        const double L[3], int R, LightBufHost& out) {
+    const int ncell = 6 * R * R;
+    std::vector<std::vector<std::pair<float, int>>> cells(ncell);
+    const double pad = 1e-4;
+    for (size_t t = 0; t < tv.size(); ++t) {
+        double q[3][3];
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int v = 0; v < 3; ++v)
+            for (int k = 0; k < 3; ++k) {
+                q[v][k] = tv[t][3 * v + k] - L[k];
+                lo[k] = std::min(lo[k], tv[t][3 * v + k]);
+                hi[k] = std::max(hi[k], tv[t][3 * v + k]);
+            }
+        double dd = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double e = std::max(std::max(lo[k] - L[k], L[k] - hi[k]), 0.0);
+            dd += e * e;
+        }
+        float dmin = (float)(std::sqrt(dd) * (1.0 - 1e-6));
+        dmin = std::nextafter(dmin, 0.0f);
+        for (int face = 0; face < 6; ++face) {
+            int axis = face / 2;
+            double sg = (face & 1) ? -1.0 : 1.0;
+            int ia = (axis + 1) % 3, ib = (axis + 2) % 3;
+            std::vector<std::array<double, 3>> poly;   // (m, a, b)
+            for (int v = 0; v < 3; ++v) poly.push_back({sg * q[v][axis], q[v][ia], q[v][ib]});
+            // clip against m - a >= 0, m + a >= 0, m - b >= 0, m + b >= 0
+            const double pl[4][3] = {{1, -1, 0}, {1, 1, 0}, {1, 0, -1}, {1, 0, 1}};
+            for (int p = 0; p < 4 && !poly.empty(); ++p) {
+                std::vector<std::array<double, 3>> o;
+                size_t n = poly.size();
+                for (size_t i = 0; i < n; ++i) {
+                    const auto& A = poly[i];
+                    const auto& B = poly[(i + 1) % n];
+                    double da = pl[p][0] * A[0] + pl[p][1] * A[1] + pl[p][2] * A[2];
+                    double db = pl[p][0] * B[0] + pl[p][1] * B[1] + pl[p][2] * B[2];
+                    if (da >= 0) o.push_back(A);
+                    if ((da >= 0) != (db >= 0)) {
+                        double s2 = da / (da - db);
+                        o.push_back({A[0] + s2 * (B[0] - A[0]), A[1] + s2 * (B[1] - A[1]), A[2] + s2 * (B[2] - A[2])});
+                    }
+                }
+                poly.swap(o);
+            }
+            if (poly.empty()) continue;
+            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+            bool apex = false;
+            for (const auto& P : poly) {
+                if (P[0] <= 1e-12) { apex = true; break; }
+                double u = P[1] / P[0], v = P[2] / P[0];
+                umin = std::min(umin, u); umax = std::max(umax, u);
+                vmin = std::min(vmin, v); vmax = std::max(vmax, v);
+            }
+            if (apex) { umin = vmin = -1.0; umax = vmax = 1.0; }
+            auto cidx = [&](double u) { return std::min(R - 1, std::max(0, (int)std::floor((u + 1.0) * 0.5 * R))); };
+            int i0 = cidx(umin - pad), i1 = cidx(umax + pad), j0 = cidx(vmin - pad), j1 = cidx(vmax + pad);
+            for (int i = i0; i <= i1; ++i)
+                for (int j = j0; j <= j1; ++j) cells[(face * R + i) * R + j].push_back({dmin, bvh_index[t]});
+        }
+    }
+    out.start.assign(ncell + 1, 0);
+    size_t total = 0;
+    for (int c = 0; c < ncell; ++c) {
+        out.start[c] = (int)total;
+        total += cells[c].size();
+    }
+    out.start[ncell] = (int)total;
+    out.ent.resize(total);
+    for (int c = 0; c < ncell; ++c) {
+        auto& v = cells[c];
+        std::sort(v.begin(), v.end());
+        for (size_t k = 0; k < v.size(); ++k) {
+            int bits;
+            std::memcpy(&bits, &v[k].first, sizeof(bits));
+            out.ent[out.start[c] + k] = make_int2(v[k].second, bits);
+        }
+    }
+}
+
 int upload(void** dst, const void* src, size_t bytes) {
     if (cudaMalloc(dst, bytes == 0 ? 16 : bytes) != cudaSuccess) return VRC_ERR_OOM;
     if (bytes && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return VRC_ERR_CUDA;
@@ -216,9 +311,33 @@ extern "C" int vrc_build_scene(const float* verts, int32_t n_verts, const int32_
                                           (float)(p[2][2] - p[0][2]), 0.f);
         }
     }
+    // light buffers: triangle vertices in original order, mapped to BVH leaf order
+    std::vector<LightBufHost> lbs(n_lights);
+    const int lbR = n_tris > 20000 ? 128 : 64;
+    if (n_tris > 0 && n_lights > 0) {
+        std::vector<std::array<double, 9>> tv(n_tris);
+        std::vector<int> bvh_index(n_tris);
+        for (int k = 0; k < n_tris; ++k) bvh_index[B.order[k]] = k;
+        for (int t = 0; t < n_tris; ++t)
+            for (int q = 0; q < 3; ++q)
+                for (int c = 0; c < 3; ++c) tv[t][3 * q + c] = (double)verts[3 * idx[3 * t + q] + c];
+        for (int l = 0; l < n_lights; ++l) {
+            double L[3] = {lights[l].pos[0], lights[l].pos[1], lights[l].pos[2]};
+            build_light_buffer(tv, bvh_index, L, lbR, lbs[l]);
+        }
+    }
     vrc_scene* s = (vrc_scene*)std::calloc(1, sizeof(vrc_scene));
     if (!s) return VRC_ERR_OOM;
     int rc = VRC_OK;
+    for (int l = 0; l < n_lights; ++l) {
+        if (lbs[l].start.empty()) lbs[l].start.assign(6 * lbR * lbR + 1, 0);
+        if ((rc = upload((void**)&s->d_lb_start[l], lbs[l].start.data(), lbs[l].start.size() * sizeof(int))) ||
+            (rc = upload((void**)&s->d_lb_ent[l], lbs[l].ent.data(), lbs[l].ent.size() * sizeof(int2)))) {
+            vrc_destroy_scene(s);
+            return rc;
+        }
+        s->lb_entries += (long long)lbs[l].ent.size();
+    }
     if ((rc = upload((void**)&s->d_nodes, nodes.data(), nodes.size() * sizeof(float4))) ||
         (rc = upload((void**)&s->d_tris, tris.data(), tris.size() * sizeof(float4))) ||
         (rc = upload((void**)&s->d_prim, prim.data(), prim.size() * sizeof(float4)))) {
@@ -240,7 +359,11 @@ extern "C" int vrc_build_scene(const float* verts, int32_t n_verts, const int32_
     for (int l = 0; l < n_lights; ++l) {
         d.lpos[l] = make_float3(lights[l].pos[0], lights[l].pos[1], lights[l].pos[2]);
         d.lI[l] = make_float3(lights[l].intensity[0], lights[l].intensity[1], lights[l].intensity[2]);
+        d.lb[l].start = s->d_lb_start[l];
+        d.lb[l].ent = s->d_lb_ent[l];
+        d.lb[l].R = lbR;
     }
+    d.use_lb = 1;
     d.sigma_s = medium->sigma_s;
     d.sigma_t = medium->sigma_s + medium->sigma_a;
     d.g = medium->g;
@@ -258,6 +381,10 @@ extern "C" void vrc_destroy_scene(vrc_scene* s) {
     cudaFree(s->d_prim);
     cudaFree(s->d_counter);
     cudaFree(s->h_stage_dev);
+    for (int l = 0; l < VRC_MAX_LIGHTS; ++l) {
+        cudaFree(s->d_lb_start[l]);
+        cudaFree(s->d_lb_ent[l]);
+    }
     std::free(s);
 }
 

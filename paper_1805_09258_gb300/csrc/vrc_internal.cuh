@@ -19,6 +19,17 @@
 // child >= 0: inner node index; child < 0: leaf, -(1 + (first << 3 | (count - 1))).
 // Triangles (BVH leaf order): 3 float4 = (v0, prim id bits), (e1 = v1 - v0, 0), (e2 = v2 - v0, 0).
 // Per original primitive: 3 float4 = (unit normal, 0), (albedo rgb, 0), (emission rgb, 0).
+// Light buffer (one per point light): a cube map of directions around the light,
+// R x R cells per face; cell c lists (triangle index in BVH order, lower bound of the
+// triangle's distance to the light) for every triangle whose projection from the light
+// overlaps the cell, sorted by that distance.  A shadow segment from y to the light can
+// only meet triangles listed in the cell of direction y - light that are nearer than y.
+struct DevLightBuf {
+    const int* __restrict__ start;      // [6 R R + 1]
+    const int2* __restrict__ ent;       // (tri, float bits of the distance bound)
+    int R;
+};
+
 struct DevScene {
     const float4* __restrict__ nodes;
     const float4* __restrict__ tris;
@@ -26,6 +37,8 @@ struct DevScene {
     int n_nodes, n_tris, n_lights;
     float3 lpos[VRC_MAX_LIGHTS];
     float3 lI[VRC_MAX_LIGHTS];
+    DevLightBuf lb[VRC_MAX_LIGHTS];
+    int use_lb;                         // 1: shadow rays use the light buffers
     float sigma_s, sigma_t, g;
 };
 
@@ -34,6 +47,9 @@ struct vrc_scene {
     float4* d_nodes;
     float4* d_tris;
     float4* d_prim;
+    int* d_lb_start[VRC_MAX_LIGHTS];
+    int2* d_lb_ent[VRC_MAX_LIGHTS];
+    long long lb_entries;
     int n_prims;
     vrc_record_tuning tuning;
     int sm_count;
@@ -216,6 +232,45 @@ __device__ int bvh_trace(const DevScene& sc, float3 o, float3 d, float tmin, flo
     }
     *t_hit = best_t;
     return best;
+}
+
+// cube-map cell of direction w (from the light): major axis (ties: x, then y), face =
+// 2 axis + (negative ? 1 : 0), then the two other coordinates over |major| in [-1, 1]
+__device__ __forceinline__ int lightbuf_cell(float3 w, int R) {
+    float ax = fabsf(w.x), ay = fabsf(w.y), az = fabsf(w.z);
+    int axis;
+    float m, a, b, s;
+    if (ax >= ay && ax >= az) { axis = 0; m = ax; s = w.x; a = w.y; b = w.z; }
+    else if (ay >= az) { axis = 1; m = ay; s = w.y; a = w.z; b = w.x; }
+    else { axis = 2; m = az; s = w.z; a = w.x; b = w.y; }
+    int face = 2 * axis + (s < 0.f ? 1 : 0);
+    float im = 1.0f / m;
+    int i = min(R - 1, max(0, (int)floorf((a * im + 1.0f) * 0.5f * R)));
+    int j = min(R - 1, max(0, (int)floorf((b * im + 1.0f) * 0.5f * R)));
+    return (face * R + i) * R + j;
+}
+
+// Any hit on the segment from o toward light l (unit direction ld, length dist): the same
+// triangle test as bvh_trace<true>, over the light-buffer candidates nearer than o.
+__device__ __forceinline__ bool lightbuf_occluded(const DevScene& sc, int l, float3 o, float3 ld, float dist) {
+    const DevLightBuf& L = sc.lb[l];
+    float3 w = o - sc.lpos[l];
+    int c = lightbuf_cell(w, L.R);
+    int b = __ldg(&L.start[c]), e = __ldg(&L.start[c + 1]);
+    for (int p = b; p < e; ++p) {
+        int2 en = __ldg(&L.ent[p]);
+        if (__int_as_float(en.y) >= dist) break;
+        float t;
+        int id;
+        if (tri_hit(sc.tris, en.x, o, ld, VRC_TMIN, dist, &t, &id)) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool shadow_occluded(const DevScene& sc, int l, float3 o, float3 ld, float dist) {
+    if (sc.use_lb) return lightbuf_occluded(sc, l, o, ld, dist);
+    float th;
+    return bvh_trace<true>(sc, o, ld, VRC_TMIN, dist, &th) >= 0;
 }
 
 // ------------------------------------------------------------------ Henyey-Greenstein

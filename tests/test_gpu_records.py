@@ -152,3 +152,18 @@ def test_hit_ids_agree_except_near_edges(vrc):
         same = ~bad
         assert np.allclose(g["hit_t"][:, :V][same], ref["hit_t"][:, :V][same], rtol=2e-5, atol=1e-6)
     assert mism <= 1e-4 * total + 1
+
+
+def test_light_buffer_shadow_rays_match_bvh_shadow_rays(vrc):
+    """Shadow rays through the light buffer test the same triangles with the same predicate
+    as BVH any-hit traversal: records must agree (to float summation order)."""
+    for w, n in ((W.config1(), 64), (W.config2(), 256)):
+        pos = w.positions(n)
+        a = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(shadow_bvh=0))
+        b = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(shadow_bvh=1))
+        same = np.all(a["L"] == b["L"], axis=1)
+        assert same.mean() > 0.95
+        for k in ("L", "grad", "hess"):
+            diff = np.abs(a[k] - b[k]).max(axis=1)
+            scale = np.abs(b[k]).max(axis=1) + 1e-12
+            assert np.mean(diff <= 1e-5 * scale) > 0.95, k
