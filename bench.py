@@ -353,6 +353,47 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
     return line
 
 
+def run_batching(args, w):
+    """Extra measurement (not the default line): the batching workload's records/s,
+    plain launch vs CUDA-graph replay after autotuning."""
+    import torch
+    import paper_1805_09258_gb300 as vrc
+    from paper_1805_09258_gb300 import build as vbuild
+    vbuild.build()
+    scene = vrc.Scene.from_workload(w.scene)
+    pos = torch.from_numpy(w.positions()).cuda()
+    nb = torch.from_numpy(w.band_counts).cuda()
+    out = vrc.alloc_records(pos.shape[0])
+    t0 = time.perf_counter()
+    best = vrc.autotune_records(scene, pos, w.params, out, n_bands=nb)
+    tune_s = time.perf_counter() - t0
+    graph = vrc.RecordsGraph(scene, pos, w.params, out, n_bands=nb)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for mode in ("plain", "graph"):
+        for _ in range(args.warmup):
+            graph.launch() if mode == "graph" else vrc.compute_records(scene, pos, w.params, n_bands=nb, out=out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.launch() if mode == "graph" else vrc.compute_records(scene, pos, w.params, n_bands=nb, out=out)
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        res[mode] = float(np.mean([a.elapsed_time(b) for a, b in ts]))
+    rays = float((2 * w.band_counts.astype(np.float64) ** 2 + 2).sum())
+    line = {"metric": METRIC, "value": w.n_records / (res["graph"] * 1e-3), "unit": "records/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["graph"], "higher_is_better": True,
+            "dtype": "f32 (f64 eigen-solve)", "data": "synthetic",
+            "config": {"workload": w.name, "records": w.n_records, "scene_tris": w.scene.n_tris,
+                       "primary_rays": rays, "l2": "scene 6 MB BVH; inputs 1.2 MB"},
+            "plain_ms": res["plain"], "graph_ms": res["graph"], "tuning": best, "autotune_s": tune_s,
+            "primary_rays_per_s": rays / (res["graph"] * 1e-3)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,7 +404,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batching"],
+                    help="mid (the default line) or the batching workload (extra measurement)")
     args = ap.parse_args()
+    if args.workload == "batching":
+        run_batching(args, W.config3())
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -162,6 +162,27 @@ int vrc_compute_records_host(vrc_scene* scene, const float* h_pos, int32_t n, co
 int vrc_set_record_tuning(vrc_scene* scene, const vrc_record_tuning* tuning);
 int vrc_get_record_tuning(const vrc_scene* scene, vrc_record_tuning* tuning);
 
+/* Autotuner for the record kernel's launch shape (threads per block, bands per chunk).
+ * Times each candidate on up to 16,384 of the given records (one warm-up launch and two
+ * timed launches each, CUDA events on `stream`), keeps the fastest in the scene, writes
+ * it to *best and caches it per (bands, bins, mixed-count flag, log2 of n).  A cached
+ * entry is reused without timing.  d_out is overwritten by the trial launches (its final
+ * contents are a correct evaluation of the first records).  Synchronous. */
+int vrc_autotune_records(vrc_scene* scene, const float* d_pos, int32_t n, const int32_t* d_n_bands,
+                         const vrc_record_params* params, const vrc_records_view* d_out, void* stream,
+                         vrc_record_tuning* best);
+
+/* CUDA graph of one vrc_compute_records call (work-counter reset, largest-first ordering
+ * for mixed ray counts, the persistent record kernel) with fixed buffers: replaying it
+ * recomputes the records from the current contents of d_pos / d_n_bands into d_out.
+ * The scene's current tuning is baked in.  Create is synchronous; launch is asynchronous
+ * on `stream`; the graph must be destroyed before the scene. */
+typedef struct vrc_graph vrc_graph;
+int vrc_records_graph_create(vrc_scene* scene, const float* d_pos, int32_t n, const int32_t* d_n_bands,
+                             const vrc_record_params* params, const vrc_records_view* d_out, vrc_graph** out);
+int vrc_graph_launch(vrc_graph* graph, void* stream);
+void vrc_graph_destroy(vrc_graph* graph);
+
 /* --------------------------------------------------------------- queries */
 typedef struct vrc_grid vrc_grid;
 

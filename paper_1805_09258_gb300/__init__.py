@@ -72,6 +72,11 @@ def load_library(path: Optional[str] = None):
     L.vrc_compute_records.argtypes = [P, P, I32, P, P, P, P]
     L.vrc_compute_records_host.argtypes = [P, P, I32, P, P, P, P, P, P]
     L.vrc_set_record_tuning.argtypes = [P, P]
+    L.vrc_autotune_records.argtypes = [P, P, I32, P, P, P, P, P]
+    L.vrc_records_graph_create.argtypes = [P, P, I32, P, P, P, C.POINTER(C.c_void_p)]
+    L.vrc_graph_launch.argtypes = [P, P]
+    L.vrc_graph_destroy.argtypes = [P]
+    L.vrc_graph_destroy.restype = None
     L.vrc_get_record_tuning.argtypes = [P, P]
     L.vrc_build_record_grid.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
     L.vrc_destroy_grid.argtypes = [P]
@@ -223,6 +228,42 @@ def compute_records(scene: Scene, pos, params, n_bands=None, out: Optional[dict]
                                             _stream_ptr(stream))
     _check(rc, "vrc_compute_records")
     return out
+
+
+def autotune_records(scene: Scene, pos, params, out: dict, n_bands=None, stream=None) -> dict:
+    """vrc_autotune_records: pick the record kernel's launch shape by timing; returns it."""
+    t = RecordTuning()
+    v = records_view(out)
+    p = record_params(params)
+    rc = load_library().vrc_autotune_records(scene.handle, _ptr(pos), pos.shape[0], _ptr(n_bands), C.byref(p),
+                                             C.byref(v), _stream_ptr(stream), C.byref(t))
+    _check(rc, "vrc_autotune_records")
+    return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm, shadow_bvh=t.shadow_bvh)
+
+
+class RecordsGraph:
+    """A CUDA graph of one compute_records call on fixed buffers (vrc_records_graph_create)."""
+
+    def __init__(self, scene: Scene, pos, params, out: dict, n_bands=None):
+        self._keep = (scene, pos, out, n_bands)
+        v = records_view(out)
+        p = record_params(params)
+        h = C.c_void_p()
+        rc = load_library().vrc_records_graph_create(scene.handle, _ptr(pos), pos.shape[0], _ptr(n_bands),
+                                                     C.byref(p), C.byref(v), C.byref(h))
+        _check(rc, "vrc_records_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(load_library().vrc_graph_launch(self.handle, _stream_ptr(stream)), "vrc_graph_launch")
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) and _lib is not None:
+                _lib.vrc_graph_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
 
 
 def compute_records_host(scene: Scene, pos: np.ndarray, params) -> dict:

@@ -18,6 +18,8 @@
 // in FP64 and sets the radius.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <vector>
 
 #include "vrc_internal.cuh"
 
@@ -38,6 +40,7 @@ struct RecArgs {
     int chunk_bands;             // bands per chunk
     int cap;                     // shared-memory vertex capacity per chunk
     int* counter;                // work counter (reset before the launch)
+    const int* order;            // nullable: work item -> record (largest ray sets first)
 };
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -307,7 +310,10 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
     __shared__ int s_rec;
 
     for (;;) {
-        if (tid == 0) s_rec = atomicAdd(a.counter, 1);
+        if (tid == 0) {
+            int item = atomicAdd(a.counter, 1);
+            s_rec = item < a.n ? (a.order ? a.order[item] : item) : a.n;
+        }
         __syncthreads();
         const int rec = s_rec;
         if (rec >= a.n) break;
@@ -634,7 +640,39 @@ int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
+// Largest-first order of records with uneven ray counts (longest-processing-time
+// scheduling for the persistent blocks): a counting sort by band count, descending.
+// hist has 258 ints: [0, 256] bucket counts for bands 1..256, then the running offsets.
+__global__ void k_lpt_hist(const int* n_bands, int n, int* hist) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&hist[256 - min(256, max(1, n_bands[i]))], 1);   // bucket 0 = most bands
+}
+__global__ void k_lpt_scan(int* hist) {
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 257; ++b) {
+            int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+}
+__global__ void k_lpt_scatter(const int* n_bands, int n, int* hist, int* order) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) order[atomicAdd(&hist[256 - min(256, max(1, n_bands[i]))], 1)] = i;
+}
+
 }  // namespace
+
+static int ensure_order_scratch(vrc_scene* s, int n) {
+    if (s->order_cap >= n) return VRC_OK;
+    cudaFree(s->d_order);
+    s->d_order = nullptr;
+    s->order_cap = 0;
+    if (cudaMalloc((void**)&s->d_order, sizeof(int) * ((size_t)n + 258)) != cudaSuccess) return VRC_ERR_OOM;
+    s->order_cap = n;
+    return VRC_OK;
+}
 
 extern "C" int vrc_set_record_tuning(vrc_scene* s, const vrc_record_tuning* t) {
     if (!s || !t) return VRC_ERR_INVALID;
@@ -692,7 +730,20 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.chunk_bands = cb;
     a.cap = cap;
     a.counter = s->d_counter;
+    a.order = nullptr;
     VRC_CUDA_CHECK(cudaMemsetAsync(s->d_counter, 0, sizeof(int), st));
+    if (d_n_bands && n > 1) {
+        // largest ray sets first; the order and histogram live in scene-owned scratch
+        int rc = ensure_order_scratch(s, n);
+        if (rc != VRC_OK) return rc;
+        int* hist = s->d_order + n;
+        VRC_CUDA_CHECK(cudaMemsetAsync(hist, 0, sizeof(int) * 258, st));
+        int nbk = (n + 255) / 256;
+        k_lpt_hist<<<nbk, 256, 0, st>>>(d_n_bands, n, hist);
+        k_lpt_scan<<<1, 32, 0, st>>>(hist);
+        k_lpt_scatter<<<nbk, 256, 0, st>>>(d_n_bands, n, hist, s->d_order);
+        a.order = s->d_order;
+    }
     switch (nt) {
         case 128: return launch_records<128>(s, a, smem, st);
         case 512: return launch_records<512>(s, a, smem, st);
@@ -734,4 +785,115 @@ extern "C" int vrc_compute_records_host(vrc_scene* s, const float* h_pos, int32_
     if (h_status) VRC_CUDA_CHECK(cudaMemcpy(h_status, v.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
     VRC_CUDA_CHECK(cudaDeviceSynchronize());
     return VRC_OK;
+}
+
+// ----------------------------------------------------------------- CUDA graph
+struct vrc_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" int vrc_records_graph_create(vrc_scene* s, const float* d_pos, int32_t n, const int32_t* d_n_bands,
+                                        const vrc_record_params* p, const vrc_records_view* out, vrc_graph** g) {
+    if (!s || !p || !out || !g || n < 1) return VRC_ERR_INVALID;
+    *g = nullptr;
+    if (d_n_bands) {
+        int rc = ensure_order_scratch(s, n);     // no allocation may happen inside the capture
+        if (rc != VRC_OK) return rc;
+    }
+    cudaStream_t cs;
+    VRC_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    vrc_graph* G = new vrc_graph();
+    int rc = VRC_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = VRC_ERR_CUDA;
+    if (rc == VRC_OK) {
+        int rc2 = vrc_compute_records(s, d_pos, n, d_n_bands, p, out, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &G->graph);
+        if (rc2 != VRC_OK) rc = rc2;
+        else if (e != cudaSuccess) rc = VRC_ERR_CUDA;
+    }
+    if (rc == VRC_OK && cudaGraphInstantiate(&G->exec, G->graph, 0) != cudaSuccess) rc = VRC_ERR_CUDA;
+    cudaStreamDestroy(cs);
+    if (rc != VRC_OK) {
+        if (G->graph) cudaGraphDestroy(G->graph);
+        delete G;
+        cudaGetLastError();
+        return rc;
+    }
+    *g = G;
+    return VRC_OK;
+}
+
+extern "C" int vrc_graph_launch(vrc_graph* g, void* stream) {
+    if (!g) return VRC_ERR_INVALID;
+    return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" void vrc_graph_destroy(vrc_graph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+// ----------------------------------------------------------------- autotuner
+namespace {
+struct TuneEntry {
+    int nb, ns, mixed, logn;
+    vrc_record_tuning t;
+};
+std::mutex g_tune_mutex;
+std::vector<TuneEntry> g_tune_cache;
+}  // namespace
+
+extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n, const int32_t* d_n_bands,
+                                    const vrc_record_params* p, const vrc_records_view* out, void* stream,
+                                    vrc_record_tuning* best) {
+    if (!s || !p || !out || n < 1) return VRC_ERR_INVALID;
+    int logn = 0;
+    while ((1 << (logn + 1)) <= n) ++logn;
+    const int mixed = d_n_bands ? 1 : 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (const TuneEntry& e : g_tune_cache)
+            if (e.nb == p->n_bands && e.ns == p->n_bins && e.mixed == mixed && e.logn == logn) {
+                s->tuning = e.t;
+                if (best) *best = e.t;
+                return VRC_OK;
+            }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int m = n < 16384 ? n : 16384;
+    vrc_record_tuning saved = s->tuning, top = saved;
+    float top_ms = 3.0e38f;
+    cudaEvent_t e0, e1;
+    VRC_CUDA_CHECK(cudaEventCreate(&e0));
+    VRC_CUDA_CHECK(cudaEventCreate(&e1));
+    const int threads[3] = {128, 256, 512};
+    const int chunks[4] = {0, 8, 16, 32};
+    for (int ti = 0; ti < 3; ++ti)
+        for (int ci = 0; ci < 4; ++ci) {
+            if (chunks[ci] >= p->n_bands) continue;
+            vrc_record_tuning t = saved;
+            t.threads = threads[ti];
+            t.chunk_bands = chunks[ci];
+            t.blocks_per_sm = 0;
+            s->tuning = t;
+            if (vrc_compute_records(s, d_pos, m, d_n_bands, p, out, stream) != VRC_OK) continue;
+            cudaEventRecord(e0, st);
+            bool ok = true;
+            for (int r = 0; r < 2 && ok; ++r) ok = vrc_compute_records(s, d_pos, m, d_n_bands, p, out, stream) == VRC_OK;
+            cudaEventRecord(e1, st);
+            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < top_ms) { top_ms = ms; top = t; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->tuning = top;
+    if (best) *best = top;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.push_back({p->n_bands, p->n_bins, mixed, logn, top});
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }

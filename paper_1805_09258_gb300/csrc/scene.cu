@@ -380,6 +380,7 @@ extern "C" void vrc_destroy_scene(vrc_scene* s) {
     cudaFree(s->d_tris);
     cudaFree(s->d_prim);
     cudaFree(s->d_counter);
+    cudaFree(s->d_order);
     cudaFree(s->h_stage_dev);
     for (int l = 0; l < VRC_MAX_LIGHTS; ++l) {
         cudaFree(s->d_lb_start[l]);

@@ -54,6 +54,8 @@ struct vrc_scene {
     vrc_record_tuning tuning;
     int sm_count;
     int* d_counter;       // persistent-launch work counter (one int)
+    int* d_order;         // largest-first record order + histogram (grown on demand)
+    int order_cap;
     // device staging for vrc_compute_records_host (grown on demand)
     float* h_stage_dev;
     size_t h_stage_floats;
