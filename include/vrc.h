@@ -203,6 +203,45 @@ void vrc_destroy_grid(vrc_grid* grid);
 int vrc_query_inscatter(const vrc_grid* grid, const float* d_q, int32_t nq, float* d_rgb, int32_t* d_status,
                         void* stream);
 
+/* --------------------------------------------------------------- learned radius
+ * Not in the paper: a small network predicts a record's log validity radius from a cheap
+ * coarse ray set, so full records are computed only where they are needed; the full
+ * record remains the judge (its radius decides coverage).
+ *
+ * vrc_coarse_features: for each position d_pos[i], the coarse stratified ray set of
+ * `params` (n_bands x n_bins, jitter seed, rec_base; pole rays excluded) gives
+ * d_feat[i][v] = log(distance to the first hit or the cube exit) and
+ * d_feat[i][N + v] = sum over lights of transmittance x visibility from that point,
+ * N = n_bands * n_bins (N = 128 for the network's 256 inputs).  Asynchronous. */
+int vrc_coarse_features(vrc_scene* scene, const float* d_pos, int32_t n, const vrc_record_params* params,
+                        float* d_feat, void* stream);
+
+/* The network: 256 -> 64 -> GELU -> 64 -> GELU -> 1 (log radius), BF16 weights and
+ * activations as tensor-core operands, FP32 accumulation.  Parameters are one float
+ * vector of vrc_mlp_num_params() = 20,673 values: W1 [64][256], b1 [64], W2 [64][64],
+ * b2 [64], w3 [64], b3 [1]; the library keeps an FP32 master copy and AdamW moments.
+ * create copies the initial parameters (host, required: the caller draws them);
+ * get/set copy parameters, moments and step count (checkpoint and resume; moments may be
+ * NULL).  predict: d_logr[n] from d_feat[n][256] (16-byte aligned).  gradient: the MSE
+ * loss gradient over the n examples into d_grad (NULL: internal buffer) and, optionally,
+ * the predictions into d_pred.  train_step: gradient + one AdamW step (betas 0.9, 0.999,
+ * eps 1e-8, decoupled weight decay); *h_loss (nullable, then synchronous) = mean squared
+ * residual before the step.  status reports VRC_ERR_TIMEOUT if a bounded device wait of a
+ * tensor-core kernel gave up. */
+typedef struct vrc_mlp vrc_mlp;
+int vrc_mlp_create(const float* h_params, vrc_mlp** out);
+void vrc_mlp_destroy(vrc_mlp* mlp);
+int32_t vrc_mlp_num_params(void);
+int vrc_mlp_get_params(const vrc_mlp* mlp, float* h_params, float* h_adam_m, float* h_adam_v, int64_t* h_step);
+int vrc_mlp_set_params(vrc_mlp* mlp, const float* h_params, const float* h_adam_m, const float* h_adam_v,
+                       int64_t step);
+int vrc_mlp_predict(const vrc_mlp* mlp, const float* d_feat, int32_t n, float* d_logr, void* stream);
+int vrc_mlp_gradient(vrc_mlp* mlp, const float* d_feat, const float* d_target, int32_t n, float* d_grad,
+                     float* d_pred, void* stream);
+int vrc_mlp_train_step(vrc_mlp* mlp, const float* d_feat, const float* d_target, int32_t n, float lr,
+                       float weight_decay, float* h_loss, void* stream);
+int vrc_mlp_status(const vrc_mlp* mlp);
+
 /* Queries for callers that cannot allocate device memory.
  *
  * No counterpart in the paper: this is a library convenience.  vrc_query_inscatter

@@ -93,6 +93,7 @@ def lib():
         _lib.orc_cell_vertices.argtypes = [C.c_int, C.c_int, C.c_int, P]
         _lib.orc_trace.argtypes = [P, P, P, C.c_int, P, P, P, P]
         _lib.orc_query.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P, P, P]
+        _lib.orc_coarse_features.argtypes = [P, P, P, P, C.c_int, P, P]
     return _lib
 
 
@@ -308,3 +309,18 @@ def query(rec_pos, rec_R, rec_L, rec_grad, rec_hess, q, order: int = 1):
     lib().orc_query(_p(rec_pos), _p(rec_R), _p(rec_L), _p(rec_grad), _p(rec_hess), rec_pos.shape[0], _p(q),
                     nq, order, _p(out), _p(st), _p(near))
     return out, st, near
+
+
+def coarse_features(oscene: OracleScene, rp, pos, rec_ids=None):
+    """Features of the learned radius predictor for each position: log hit distance and
+    to-light transmittance x visibility of the coarse ray set.  Returns (features [n, 2N],
+    near-tie flags [n, 2N])."""
+    pos = _f32(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    N = rp.n_bands * rp.n_bins
+    ids = None if rec_ids is None else np.ascontiguousarray(rec_ids, dtype=np.int64)
+    out = np.zeros((n, 2 * N))
+    unc = np.zeros((n, 2 * N), np.uint8)
+    p = make_params(rp)
+    lib().orc_coarse_features(oscene.ptr, C.byref(p), _p(pos), _p(ids), n, _p(out), _p(unc))
+    return out, unc.astype(bool)

@@ -1399,3 +1399,49 @@ int orc_query(const double* rpos, const double* rR, const double* rL, const doub
 }
 
 int orc_out_stride(void) { return ORC_OUT_STRIDE; }
+
+/* ------------------------------------------------ coarse features (learned radius) */
+/* Not in the paper: the input of the learned radius predictor.  For the coarse ray set
+ * (rays v < N of the n_bands x n_bins strata, jitter from p->seed): out[v] = log(t_end),
+ * the distance to the first hit or to the cube exit; out[N + v] = sum over lights of
+ * T(y, light) V(y, light) at y = x + t_end d (hit points start their shadow ray 1e-5 along
+ * the normal facing x, exit points start at y).  unc[v] / unc[N + v] (nullable) flag
+ * features whose ray or shadow ray is a near tie (within 1e-6 of an edge). */
+int orc_coarse_features(const orc_scene* s, const orc_params* p, const float* pos, const int64_t* rec_ids, int n,
+                        double* out, uint8_t* unc) {
+    int nb = p->n_bands, ns = p->n_bins, N = nb * ns;
+    for (int i = 0; i < n; ++i) {
+        v3 x = ldv(pos + 3 * i);
+        int64_t rec = rec_ids ? rec_ids[i] : p->rec_base + i;
+        for (int v = 0; v < N; ++v) {
+            v3 d = ray_direction(p, nb, ns, rec, v);
+            double t, mg = INFINITY, tie = INFINITY, tv = INFINITY;
+            int id = closest_hit(s, x, d, &t, &mg, &tie, &tv, 1);
+            int u_prim = mg < TIE_EDGE || tv < TIE_T;
+            if (id < 0) t = cube_exit(x, d);
+            v3 y = add(x, scl(d, t));
+            v3 o = y;
+            if (id >= 0) {
+                v3 a = ldv(s->in.tri_v + 9 * id), b = ldv(s->in.tri_v + 9 * id + 3), c = ldv(s->in.tri_v + 9 * id + 6);
+                v3 nn = cross(sub(b, a), sub(c, a));
+                nn = scl(nn, 1.0 / norm(nn));
+                if (dot(nn, d) > 0) nn = scl(nn, -1.0);
+                o = add(y, scl(nn, ORC_SHADOW_OFFSET));
+            }
+            double tv_sum = 0.0, margin = INFINITY;
+            for (int L = 0; L < s->in.n_lights; ++L) {
+                v3 pl = ldv(s->in.light_pos + 3 * L);
+                v3 lo = sub(pl, o);
+                double dl = norm(lo);
+                if (!occluded(s, o, scl(lo, 1.0 / dl), dl, &margin, 1)) tv_sum += exp(-s->sigma_t * norm(sub(pl, y)));
+            }
+            out[(size_t)i * 2 * N + v] = log(t);
+            out[(size_t)i * 2 * N + N + v] = tv_sum;
+            if (unc) {
+                unc[(size_t)i * 2 * N + v] = (uint8_t)u_prim;
+                unc[(size_t)i * 2 * N + N + v] = (uint8_t)(u_prim || margin < TIE_EDGE);
+            }
+        }
+    }
+    return 0;
+}

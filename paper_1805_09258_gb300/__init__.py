@@ -83,6 +83,17 @@ def load_library(path: Optional[str] = None):
     L.vrc_destroy_grid.restype = None
     L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
     L.vrc_query_inscatter_noalloc.argtypes = [P, I32, I32, P, I32, P, P, P]
+    L.vrc_coarse_features.argtypes = [P, P, I32, P, P, P]
+    L.vrc_mlp_create.argtypes = [P, C.POINTER(C.c_void_p)]
+    L.vrc_mlp_destroy.argtypes = [P]
+    L.vrc_mlp_destroy.restype = None
+    L.vrc_mlp_num_params.restype = I32
+    L.vrc_mlp_get_params.argtypes = [P, P, P, P, P]
+    L.vrc_mlp_set_params.argtypes = [P, P, P, P, C.c_int64]
+    L.vrc_mlp_predict.argtypes = [P, P, I32, P, P]
+    L.vrc_mlp_gradient.argtypes = [P, P, P, I32, P, P, P]
+    L.vrc_mlp_train_step.argtypes = [P, P, P, I32, C.c_float, C.c_float, P, P]
+    L.vrc_mlp_status.argtypes = [P]
     L.vrc_status_string.restype = C.c_char_p
     L.vrc_status_string.argtypes = [C.c_int]
     _lib = L
@@ -346,3 +357,82 @@ def query_inscatter_noalloc(records: dict, q, n: Optional[int] = None, extrap_or
                                                     _ptr(status), _stream_ptr(stream))
     _check(rc, "vrc_query_inscatter_noalloc")
     return rgb, status
+
+
+def coarse_features(scene: Scene, pos, params, out=None, stream=None):
+    """vrc_coarse_features: [n, 2 N] float32 features of the coarse ray set at `pos`."""
+    torch = _torch()
+    n = pos.shape[0]
+    N = int(params.n_bands) * int(params.n_bins)
+    if out is None:
+        out = torch.empty((n, 2 * N), dtype=torch.float32, device=pos.device)
+    p = record_params(params)
+    _check(load_library().vrc_coarse_features(scene.handle, _ptr(pos), n, C.byref(p), _ptr(out),
+                                              _stream_ptr(stream)), "vrc_coarse_features")
+    return out
+
+
+class MLP:
+    """The learned radius predictor (vrc_mlp_*): 256-64-64-1 GELU network on tensor cores."""
+
+    def __init__(self, params: np.ndarray):
+        L = load_library()
+        self.n_params = int(L.vrc_mlp_num_params())
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        assert params.size == self.n_params
+        h = C.c_void_p()
+        _check(L.vrc_mlp_create(params.ctypes.data, C.byref(h)), "vrc_mlp_create")
+        self.handle = h
+
+    def get_params(self, with_moments: bool = False):
+        p = np.zeros(self.n_params, np.float32)
+        m = np.zeros(self.n_params, np.float32) if with_moments else None
+        v = np.zeros(self.n_params, np.float32) if with_moments else None
+        step = C.c_int64(0)
+        _check(load_library().vrc_mlp_get_params(self.handle, p.ctypes.data, None if m is None else m.ctypes.data,
+                                                 None if v is None else v.ctypes.data, C.byref(step)),
+               "vrc_mlp_get_params")
+        return (p, m, v, step.value) if with_moments else p
+
+    def set_params(self, p, m=None, v=None, step: int = 0):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        m = None if m is None else np.ascontiguousarray(m, dtype=np.float32)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+        _check(load_library().vrc_mlp_set_params(self.handle, p.ctypes.data, None if m is None else m.ctypes.data,
+                                                 None if v is None else v.ctypes.data, step), "vrc_mlp_set_params")
+
+    def predict(self, feat, out=None, stream=None):
+        torch = _torch()
+        n = feat.shape[0]
+        if out is None:
+            out = torch.empty((n,), dtype=torch.float32, device=feat.device)
+        _check(load_library().vrc_mlp_predict(self.handle, _ptr(feat), n, _ptr(out), _stream_ptr(stream)),
+               "vrc_mlp_predict")
+        return out
+
+    def gradient(self, feat, target, stream=None):
+        torch = _torch()
+        g = torch.empty((self.n_params,), dtype=torch.float32, device=feat.device)
+        pred = torch.empty((feat.shape[0],), dtype=torch.float32, device=feat.device)
+        _check(load_library().vrc_mlp_gradient(self.handle, _ptr(feat), _ptr(target), feat.shape[0], _ptr(g),
+                                               _ptr(pred), _stream_ptr(stream)), "vrc_mlp_gradient")
+        return g, pred
+
+    def train_step(self, feat, target, lr: float, weight_decay: float = 1e-4, want_loss: bool = False,
+                   stream=None):
+        loss = C.c_float(0.0)
+        _check(load_library().vrc_mlp_train_step(self.handle, _ptr(feat), _ptr(target), feat.shape[0], lr,
+                                                 weight_decay, C.byref(loss) if want_loss else None,
+                                                 _stream_ptr(stream)), "vrc_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def status(self) -> int:
+        return int(load_library().vrc_mlp_status(self.handle))
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) and _lib is not None:
+                _lib.vrc_mlp_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
