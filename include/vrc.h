@@ -108,6 +108,7 @@ typedef struct {
  *   n_cells [n]     cells evaluated (lit cells of all shells; work counter), NULL to skip
  *   n_far [n]       furthest-vertex evaluations (sum of tie sizes over lit cells), NULL to skip
  *   n_shells [n]    medium shells K = ceil(max t_end / dt), NULL to skip
+ *   log_radius [n]  natural log of the radius (training target of the learned predictor), NULL to skip
  *   hit_prim, hit_t [n][dbg_stride]  per-ray primary hit id (-1 = escaped) and t,
  *                   for rays v < n_bands*n_bins + 2; NULL to skip */
 typedef struct {
@@ -129,6 +130,7 @@ typedef struct {
     int32_t* n_cells;
     int32_t* n_far;
     int32_t* n_shells;
+    float* log_radius;
     int32_t* hit_prim;
     float* hit_t;
     int32_t dbg_stride;
@@ -202,6 +204,48 @@ void vrc_destroy_grid(vrc_grid* grid);
  * Asynchronous on `stream`. */
 int vrc_query_inscatter(const vrc_grid* grid, const float* d_q, int32_t nq, float* d_rgb, int32_t* d_status,
                         void* stream);
+
+/* --------------------------------------------------------------- renderer
+ * The renderer around the cache (Sec. 6): camera rays marched through the medium with the
+ * paper's uniform ray marching, cache look-ups at the march points, adaptive placement.
+ * Camera: pinhole at pos looking along forward (up = +z), vertical field of view in
+ * degrees, width x height pixels.  A pixel's ray is marched from its entry into the unit
+ * cube to min(first hit, cube exit) in `steps` equal segments; the march points are the
+ * segment midpoints; a pixel's value is sum_k ds sigma_s exp(-sigma_t s_k) L(x_k). */
+typedef struct { float pos[3]; float forward[3]; float vfov_deg; int32_t width, height; } vrc_camera;
+
+/* March points of the pixels (x0 + i*stride, y0 + j*stride), i < w, j < h: d_pts
+ * [w*h*steps][3] (pixel-major, then step), d_valid [w*h*steps] (0 where the pixel's ray
+ * misses the medium).  Asynchronous. */
+int vrc_march_points(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                     int32_t stride, int32_t steps, float* d_pts, int32_t* d_valid, void* stream);
+
+/* Render the w x h pixel rectangle at (x0, y0) from an order-1 grid: d_img [w*h][3]; d_miss
+ * [w*h] (nullable) = march points of the pixel that no record covers (they contribute 0).
+ * Asynchronous. */
+int vrc_render(vrc_scene* scene, const vrc_grid* grid, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w,
+               int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
+
+/* Pixel values from caller-given radiance at every march point (d_L [w*h*steps][3], in
+ * vrc_march_points order) -- e.g. a full record at every point, the reference image. */
+int vrc_composite(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                  int32_t steps, const float* d_L, float* d_img, void* stream);
+
+/* Placement wave (Sec. 6: a record is added where no valid record exists): among the
+ * candidates with 0 <= d_level[i] <= level, pick in each cell of a 2^level grid over the
+ * cube the one with the smallest index.  Writes the picked indices (ascending) and their
+ * positions to d_site_idx / d_site_pts and their number to *h_count (synchronous).
+ * d_scratch must hold 8^level + 2 n + n/1024 + 2 ints; level <= 8. */
+int vrc_select_sites(const float* d_pts, const int32_t* d_level, int32_t n, int32_t level, int32_t* d_scratch,
+                     int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts, int32_t* h_count, void* stream);
+
+/* d_level[i] = -1 (leaves the candidate pool) where d_count[i] > 0.  Asynchronous. */
+int vrc_update_coverage(const int32_t* d_count, int32_t n, int32_t* d_level, void* stream);
+
+/* Learned placement level of each pool candidate from a predicted log radius: the finest
+ * level whose cell is at most cell_over_radius x the predicted radius, in [lmin, lmax]. */
+int vrc_levels_from_radius(const float* d_logr, int32_t n, float cell_over_radius, int32_t lmin, int32_t lmax,
+                           int32_t* d_level, void* stream);
 
 /* --------------------------------------------------------------- learned radius
  * Not in the paper: a small network predicts a record's log validity radius from a cheap

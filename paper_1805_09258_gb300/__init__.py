@@ -45,7 +45,7 @@ class RecordParamsC(C.Structure):
 class RecordsView(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms",
                                            "hess_ms", "L_ff", "radius", "eig", "kappa", "status", "pos",
-                                           "n_cells", "n_far", "n_shells", "hit_prim", "hit_t")] + [("dbg_stride", C.c_int32)]
+                                           "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t")] + [("dbg_stride", C.c_int32)]
 
 
 class RecordTuning(C.Structure):
@@ -84,6 +84,12 @@ def load_library(path: Optional[str] = None):
     L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
     L.vrc_query_inscatter_noalloc.argtypes = [P, I32, I32, P, I32, P, P, P]
     L.vrc_coarse_features.argtypes = [P, P, I32, P, P, P]
+    L.vrc_march_points.argtypes = [P, P, I32, I32, I32, I32, I32, I32, P, P, P]
+    L.vrc_render.argtypes = [P, P, P, I32, I32, I32, I32, I32, P, P, P]
+    L.vrc_composite.argtypes = [P, P, I32, I32, I32, I32, I32, P, P, P]
+    L.vrc_select_sites.argtypes = [P, P, I32, I32, P, C.c_int64, P, P, P, P]
+    L.vrc_update_coverage.argtypes = [P, I32, P, P]
+    L.vrc_levels_from_radius.argtypes = [P, I32, C.c_float, I32, I32, P, P]
     L.vrc_mlp_create.argtypes = [P, C.POINTER(C.c_void_p)]
     L.vrc_mlp_destroy.argtypes = [P]
     L.vrc_mlp_destroy.restype = None
@@ -208,7 +214,7 @@ def alloc_records(n: int, full: bool = True, device="cuda"):
 def records_view(out: dict, dbg_stride: int = 0) -> RecordsView:
     v = RecordsView()
     for k in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms", "hess_ms", "L_ff", "radius",
-              "eig", "kappa", "status", "pos", "n_cells", "n_far", "n_shells", "hit_prim", "hit_t"):
+              "eig", "kappa", "status", "pos", "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t"):
         setattr(v, k, _ptr(out.get(k)))
     v.dbg_stride = dbg_stride
     return v
@@ -436,3 +442,63 @@ class MLP:
                 self.handle = None
         except Exception:
             pass
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("forward", C.c_float * 3), ("vfov_deg", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32)]
+
+    @classmethod
+    def make(cls, pos, forward, vfov_deg, width, height):
+        c = cls()
+        c.pos[:] = [float(v) for v in pos]
+        c.forward[:] = [float(v) for v in forward]
+        c.vfov_deg, c.width, c.height = float(vfov_deg), int(width), int(height)
+        return c
+
+
+def march_points(scene: Scene, cam: Camera, x0, y0, w, h, stride, steps, stream=None):
+    torch = _torch()
+    n = w * h * steps
+    pts = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    valid = torch.empty((n,), dtype=torch.int32, device="cuda")
+    _check(load_library().vrc_march_points(scene.handle, C.byref(cam), x0, y0, w, h, stride, steps, _ptr(pts),
+                                           _ptr(valid), _stream_ptr(stream)), "vrc_march_points")
+    return pts, valid
+
+
+def render(scene: Scene, grid: "Grid", cam: Camera, x0, y0, w, h, steps, img=None, miss=None, stream=None):
+    torch = _torch()
+    if img is None:
+        img = torch.empty((w * h, 3), dtype=torch.float32, device="cuda")
+    if miss is None:
+        miss = torch.empty((w * h,), dtype=torch.int32, device="cuda")
+    _check(load_library().vrc_render(scene.handle, grid.handle, C.byref(cam), x0, y0, w, h, steps, _ptr(img),
+                                     _ptr(miss), _stream_ptr(stream)), "vrc_render")
+    return img, miss
+
+
+def composite(scene: Scene, cam: Camera, x0, y0, w, h, steps, L, stream=None):
+    torch = _torch()
+    img = torch.empty((w * h, 3), dtype=torch.float32, device="cuda")
+    _check(load_library().vrc_composite(scene.handle, C.byref(cam), x0, y0, w, h, steps, _ptr(L), _ptr(img),
+                                        _stream_ptr(stream)), "vrc_composite")
+    return img
+
+
+def select_sites(pts, level, wave_level: int, scratch, site_idx, site_pts, stream=None) -> int:
+    cnt = C.c_int32(0)
+    _check(load_library().vrc_select_sites(_ptr(pts), _ptr(level), pts.shape[0], wave_level, _ptr(scratch),
+                                           scratch.numel(), _ptr(site_idx), _ptr(site_pts), C.byref(cnt),
+                                           _stream_ptr(stream)), "vrc_select_sites")
+    return int(cnt.value)
+
+
+def update_coverage(count, level, stream=None):
+    _check(load_library().vrc_update_coverage(_ptr(count), count.shape[0], _ptr(level), _stream_ptr(stream)),
+           "vrc_update_coverage")
+
+
+def levels_from_radius(logr, level, cell_over_radius: float, lmin: int, lmax: int, stream=None):
+    _check(load_library().vrc_levels_from_radius(_ptr(logr), logr.shape[0], cell_over_radius, lmin, lmax,
+                                                 _ptr(level), _stream_ptr(stream)), "vrc_levels_from_radius")

@@ -14,24 +14,6 @@
 
 #include "vrc_internal.cuh"
 
-struct vrc_grid {
-    int n;                 // records
-    int G;                 // cells per axis
-    int order;             // 1 or 2
-    float4* rec;           // [n][4]: (pos, R), (L, g_r.x), (g_r.y, g_r.z, g_g.x, g_g.y), (g_g.z, g_b)
-    float4* hess;          // [n][5]: 18 Hessian entries (order 2), padded
-    int* cell_start;       // [G^3 + 1]
-    int* cell_list;        // [entries]
-    long long entries;
-    // query scratch (grown on demand)
-    int* q_cell;           // [cap]
-    int* q_rank;           // [cap]
-    int* q_perm;           // [cap]
-    int* q_count;          // [G^3 + 1]
-    int* scan_tmp;         // block sums
-    int q_cap;
-};
-
 namespace {
 
 constexpr int SCAN_BLOCK = 1024;

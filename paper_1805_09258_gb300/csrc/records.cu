@@ -598,6 +598,7 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
             }
             if (tot[31] + tot[63] > 0.f) status |= VRC_REC_DEGENERATE;
             o.radius[rec] = (float)R;
+            if (o.log_radius) o.log_radius[rec] = (float)log(R);
             o.status[rec] = status;
             if (o.n_cells) o.n_cells[rec] = misc[1];
             if (o.n_far) o.n_far[rec] = misc[3];

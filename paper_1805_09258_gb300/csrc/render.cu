@@ -1,0 +1,346 @@
+// render.cu -- the renderer around the cache (Sec. 6): camera rays marched through the
+// medium, cache look-ups at the march points, and adaptive record placement.
+//
+// Camera: pinhole at `pos` looking along `forward` (up = +z), vertical field of view
+// `vfov_deg`, width x height pixels.  A pixel's ray enters the unit cube at s_in and is
+// marched to s_end = min(first hit, cube exit) in `steps` equal segments; the march points
+// are the segment midpoints (the paper's uniform ray marching, Sec. 6).  A pixel's value
+// is sum_k ds sigma_s exp(-sigma_t (s_k - s_in)) L(x_k), L from Eq. radianceTaylor.
+//
+// Placement (Sec. 6: records are added where no valid record covers a point): candidates
+// carry a level; wave `level` picks, in every cell of a 2^level grid over the cube, the
+// uncovered candidate with the smallest index among those whose level is <= `level`.
+// Full records are computed at the picked sites, the grid is rebuilt, the candidates are
+// queried, and covered candidates leave the pool.
+#include <algorithm>
+#include <cmath>
+
+#include "vrc_internal.cuh"
+
+namespace {
+
+struct Cam {
+    float3 pos, fwd, right, up;
+    float tan_half, aspect;
+    int W, H;
+};
+
+__device__ __forceinline__ float3 norm3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+
+__device__ __forceinline__ float3 cam_dir(const Cam& c, int px, int py) {
+    float x = (2.0f * ((float)px + 0.5f) / (float)c.W - 1.0f) * c.tan_half * c.aspect;
+    float y = (1.0f - 2.0f * ((float)py + 0.5f) / (float)c.H) * c.tan_half;
+    return norm3(c.fwd + c.right * x + c.up * y);
+}
+
+// [s_in, s_out] of the ray in the unit cube; false if it misses
+__device__ __forceinline__ bool cube_span(float3 o, float3 d, float& s_in, float& s_out) {
+    float t0 = -3.0e38f, t1 = 3.0e38f;
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (dd[k] == 0.f) {
+            if (oo[k] < 0.f || oo[k] > 1.f) return false;
+            continue;
+        }
+        float a = (0.f - oo[k]) / dd[k], b = (1.f - oo[k]) / dd[k];
+        t0 = fmaxf(t0, fminf(a, b));
+        t1 = fminf(t1, fmaxf(a, b));
+    }
+    s_in = fmaxf(t0, 0.f);
+    s_out = t1;
+    return s_out > s_in;
+}
+
+// march span of pixel (px, py): entry, step and validity
+__device__ __forceinline__ bool pixel_span(const DevScene& sc, const Cam& c, int px, int py, int steps, float3& o,
+                                           float3& d, float& s_in, float& ds) {
+    o = c.pos;
+    d = cam_dir(c, px, py);
+    float s_out;
+    if (!cube_span(o, d, s_in, s_out)) return false;
+    float3 e = o + d * s_in;
+    float th;
+    int prim = bvh_trace<false>(sc, e, d, VRC_TMIN, s_out - s_in + 1e-4f, &th);
+    float len = prim >= 0 ? th : (s_out - s_in);
+    if (!(len > 0.f)) return false;
+    ds = len / (float)steps;
+    return true;
+}
+
+__global__ void k_march_points(DevScene sc, Cam c, int x0, int y0, int w, int h, int stride, int steps, float* pts,
+                               int* valid) {
+    long long total = (long long)w * h * steps;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int k = (int)(i % steps);
+        long long pix = i / steps;
+        int px = x0 + (int)(pix % w) * stride, py = y0 + (int)(pix / w) * stride;
+        float3 o, d;
+        float s_in, ds;
+        bool ok = px < c.W && py < c.H && pixel_span(sc, c, px, py, steps, o, d, s_in, ds);
+        float3 x = ok ? o + d * (s_in + ((float)k + 0.5f) * ds) : f3(0.f, 0.f, 0.f);
+        pts[3 * i] = x.x;
+        pts[3 * i + 1] = x.y;
+        pts[3 * i + 2] = x.z;
+        valid[i] = ok ? 1 : 0;
+    }
+}
+
+// Eq. radianceTaylor at x from the grid's compact records (order 1)
+struct GridView {
+    const float4* rec;
+    const int* start;
+    const int* list;
+    int G;
+};
+
+__device__ __forceinline__ float3 cache_lookup(const GridView& g, float3 x, int& cnt) {
+    int ix = min(g.G - 1, max(0, (int)floorf(x.x * g.G)));
+    int iy = min(g.G - 1, max(0, (int)floorf(x.y * g.G)));
+    int iz = min(g.G - 1, max(0, (int)floorf(x.z * g.G)));
+    int cell = (ix * g.G + iy) * g.G + iz;
+    int b = __ldg(&g.start[cell]), e = __ldg(&g.start[cell + 1]);
+    float ar = 0.f, ag = 0.f, ab = 0.f, sw = 0.f;
+    cnt = 0;
+    for (int p = b; p < e; ++p) {
+        int k = __ldg(&g.list[p]);
+        float4 a = __ldg(&g.rec[4 * k]);
+        float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
+        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(d2 < a.w * a.w)) continue;
+        float4 r1 = __ldg(&g.rec[4 * k + 1]), r2 = __ldg(&g.rec[4 * k + 2]), r3 = __ldg(&g.rec[4 * k + 3]);
+        float dd = 1.0f - sqrtf(d2) / a.w;
+        float w = dd * dd * fmaf(-2.0f, dd, 3.0f);
+        ar = fmaf(w, r1.x + fmaf(r1.w, dx, fmaf(r2.x, dy, r2.y * dz)), ar);
+        ag = fmaf(w, r1.y + fmaf(r2.z, dx, fmaf(r2.w, dy, r3.x * dz)), ag);
+        ab = fmaf(w, r1.z + fmaf(r3.y, dx, fmaf(r3.z, dy, r3.w * dz)), ab);
+        sw += w;
+        ++cnt;
+    }
+    float inv = cnt ? 1.0f / sw : 0.f;
+    return f3(ar * inv, ag * inv, ab * inv);
+}
+
+// one thread per pixel: march, look up, accumulate; misses counted per pixel
+__global__ void k_render(DevScene sc, Cam c, GridView g, int x0, int y0, int w, int h, int steps, float* img,
+                         int* miss) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w * h) return;
+    int px = x0 + i % w, py = y0 + i / w;
+    float3 o, d, acc = f3(0.f, 0.f, 0.f);
+    float s_in, ds;
+    int nmiss = 0;
+    if (px < c.W && py < c.H && pixel_span(sc, c, px, py, steps, o, d, s_in, ds)) {
+        for (int k = 0; k < steps; ++k) {
+            float s = ((float)k + 0.5f) * ds;
+            float3 x = o + d * (s_in + s);
+            int cnt;
+            float3 L = cache_lookup(g, x, cnt);
+            if (cnt == 0) ++nmiss;
+            acc = acc + L * (ds * sc.sigma_s * __expf(-sc.sigma_t * s));
+        }
+    }
+    img[3 * i] = acc.x;
+    img[3 * i + 1] = acc.y;
+    img[3 * i + 2] = acc.z;
+    if (miss) miss[i] = nmiss;
+}
+
+// pixel values from per-point radiance (for the reference image: L at every march point)
+__global__ void k_composite(DevScene sc, Cam c, int x0, int y0, int w, int h, int steps, const float* L, float* img) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w * h) return;
+    int px = x0 + i % w, py = y0 + i / w;
+    float3 o, d, acc = f3(0.f, 0.f, 0.f);
+    float s_in, ds;
+    if (px < c.W && py < c.H && pixel_span(sc, c, px, py, steps, o, d, s_in, ds))
+        for (int k = 0; k < steps; ++k) {
+            float s = ((float)k + 0.5f) * ds;
+            const float* l = L + 3 * ((size_t)i * steps + k);
+            acc = acc + f3(l[0], l[1], l[2]) * (ds * sc.sigma_s * __expf(-sc.sigma_t * s));
+        }
+    img[3 * i] = acc.x;
+    img[3 * i + 1] = acc.y;
+    img[3 * i + 2] = acc.z;
+}
+
+// ---------------------------------------------------------------- placement
+__global__ void k_site_claim(const float* pts, const int* level, int n, int lv, int G, int* cell_min) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int l = level[i];
+    if (l < 0 || l > lv) return;
+    int ix = min(G - 1, max(0, (int)floorf(pts[3 * i] * G)));
+    int iy = min(G - 1, max(0, (int)floorf(pts[3 * i + 1] * G)));
+    int iz = min(G - 1, max(0, (int)floorf(pts[3 * i + 2] * G)));
+    atomicMin(&cell_min[((size_t)ix * G + iy) * G + iz], i);
+}
+
+__global__ void k_site_flag(const float* pts, const int* level, int n, int lv, int G, const int* cell_min, int* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int l = level[i];
+    int f = 0;
+    if (l >= 0 && l <= lv) {
+        int ix = min(G - 1, max(0, (int)floorf(pts[3 * i] * G)));
+        int iy = min(G - 1, max(0, (int)floorf(pts[3 * i + 1] * G)));
+        int iz = min(G - 1, max(0, (int)floorf(pts[3 * i + 2] * G)));
+        f = cell_min[((size_t)ix * G + iy) * G + iz] == i ? 1 : 0;
+    }
+    flag[i] = f;
+}
+
+// block-local exclusive scan of flags, block totals to sums[blockIdx]
+__global__ void k_flag_scan(const int* flag, int n, int* pos, int* sums) {
+    __shared__ int s[1024];
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    int v = i < n ? flag[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) pos[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023) sums[blockIdx.x] = s[1023];
+}
+
+__global__ void k_flag_tops(int* sums, int nblk, int* total) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < nblk; ++b) {
+            int t = sums[b];
+            sums[b] = run;
+            run += t;
+        }
+        *total = run;
+    }
+}
+
+__global__ void k_gather_sites(const float* pts, const int* flag, const int* pos, const int* sums, int n,
+                               int* out_idx, float* out_pts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    int j = pos[i] + sums[i / 1024];
+    out_idx[j] = i;
+    out_pts[3 * j] = pts[3 * i];
+    out_pts[3 * j + 1] = pts[3 * i + 1];
+    out_pts[3 * j + 2] = pts[3 * i + 2];
+}
+
+__global__ void k_cover(const int* count, int n, int* level) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && count[i] > 0) level[i] = -1;
+}
+
+// learned level of a candidate from its predicted log radius: the finest level whose
+// cell is still at most `ratio` times the predicted radius, clamped to [lmin, lmax]
+__global__ void k_levels_from_logr(const float* logr, int n, float ratio, int lmin, int lmax, int* level) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || level[i] < 0) return;
+    float R = __expf(logr[i]);
+    int l = (int)ceilf(-log2f(fmaxf(ratio * R, 1e-6f)));
+    level[i] = min(lmax, max(lmin, l));
+}
+
+Cam make_cam(const float* pos, const float* fwd, float vfov_deg, int W, int H) {
+    Cam c;
+    c.pos = make_float3(pos[0], pos[1], pos[2]);
+    float fl = std::sqrt(fwd[0] * fwd[0] + fwd[1] * fwd[1] + fwd[2] * fwd[2]);
+    c.fwd = make_float3(fwd[0] / fl, fwd[1] / fl, fwd[2] / fl);
+    // right = fwd x (0,0,1), up = right x fwd
+    float rx = c.fwd.y, ry = -c.fwd.x, rz = 0.f;
+    float rl = std::sqrt(rx * rx + ry * ry);
+    if (rl < 1e-6f) { rx = 1.f; ry = 0.f; rl = 1.f; }
+    c.right = make_float3(rx / rl, ry / rl, rz);
+    c.up = make_float3(c.right.y * c.fwd.z - c.right.z * c.fwd.y, c.right.z * c.fwd.x - c.right.x * c.fwd.z,
+                       c.right.x * c.fwd.y - c.right.y * c.fwd.x);
+    c.tan_half = std::tan(0.5f * vfov_deg * 3.14159265358979f / 180.f);
+    c.aspect = (float)W / (float)H;
+    c.W = W;
+    c.H = H;
+    return c;
+}
+
+}  // namespace
+
+extern "C" int vrc_march_points(vrc_scene* s, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                                int32_t stride, int32_t steps, float* d_pts, int32_t* d_valid, void* stream) {
+    if (!s || !cam || w < 0 || h < 0 || stride < 1 || steps < 1 || !d_pts || !d_valid) return VRC_ERR_INVALID;
+    if ((long long)w * h == 0) return VRC_OK;
+    Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
+    long long total = (long long)w * h * steps;
+    int blocks = (int)std::min<long long>((total + 255) / 256, (long long)s->sm_count * 32);
+    k_march_points<<<blocks, 256, 0, (cudaStream_t)stream>>>(s->dev, c, x0, y0, w, h, stride, steps, d_pts, d_valid);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_render(vrc_scene* s, const vrc_grid* grid, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w,
+                          int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream) {
+    if (!s || !grid || !cam || w < 0 || h < 0 || steps < 1 || !d_img) return VRC_ERR_INVALID;
+    if ((long long)w * h == 0) return VRC_OK;
+    Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
+    if (grid->order != 1) return VRC_ERR_INVALID;
+    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G};
+    int n = w * h;
+    k_render<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, x0, y0, w, h, steps, d_img, d_miss);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_composite(vrc_scene* s, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                             int32_t steps, const float* d_L, float* d_img, void* stream) {
+    if (!s || !cam || w < 0 || h < 0 || steps < 1 || !d_L || !d_img) return VRC_ERR_INVALID;
+    if ((long long)w * h == 0) return VRC_OK;
+    Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
+    int n = w * h;
+    k_composite<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, x0, y0, w, h, steps, d_L, d_img);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_select_sites(const float* d_pts, const int32_t* d_level, int32_t n, int32_t level,
+                                int32_t* d_scratch, int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts,
+                                int32_t* h_count, void* stream) {
+    if (!d_pts || !d_level || n < 0 || level < 0 || level > 8 || !d_scratch || !d_site_idx || !d_site_pts || !h_count)
+        return VRC_ERR_INVALID;
+    *h_count = 0;
+    if (n == 0) return VRC_OK;
+    const int G = 1 << level;
+    const long long cells = (long long)G * G * G;
+    const int nblk = (n + 1023) / 1024;
+    if (scratch_ints < cells + 2LL * n + nblk + 1) return VRC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* cell_min = d_scratch;
+    int* flag = cell_min + cells;
+    int* pos = flag + n;
+    int* sums = pos + n;
+    VRC_CUDA_CHECK(cudaMemsetAsync(cell_min, 0x7f, sizeof(int) * cells, st));
+    int tb = 256, nb = (n + tb - 1) / tb;
+    k_site_claim<<<nb, tb, 0, st>>>(d_pts, d_level, n, level, G, cell_min);
+    k_site_flag<<<nb, tb, 0, st>>>(d_pts, d_level, n, level, G, cell_min, flag);
+    k_flag_scan<<<nblk, 1024, 0, st>>>(flag, n, pos, sums);
+    k_flag_tops<<<1, 32, 0, st>>>(sums, nblk, sums + nblk);
+    k_gather_sites<<<nb, tb, 0, st>>>(d_pts, flag, pos, sums, n, d_site_idx, d_site_pts);
+    VRC_CUDA_CHECK(cudaMemcpyAsync(h_count, sums + nblk, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    VRC_CUDA_CHECK(cudaStreamSynchronize(st));
+    return VRC_OK;
+}
+
+extern "C" int vrc_update_coverage(const int32_t* d_count, int32_t n, int32_t* d_level, void* stream) {
+    if (n < 0 || (n > 0 && (!d_count || !d_level))) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    k_cover<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_count, n, d_level);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_levels_from_radius(const float* d_logr, int32_t n, float cell_over_radius, int32_t lmin,
+                                      int32_t lmax, int32_t* d_level, void* stream) {
+    if (n < 0 || lmin < 0 || lmax < lmin || lmax > 8 || !(cell_over_radius > 0.f)) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    if (!d_logr || !d_level) return VRC_ERR_INVALID;
+    k_levels_from_logr<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_logr, n, cell_over_radius, lmin, lmax,
+                                                                          d_level);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}

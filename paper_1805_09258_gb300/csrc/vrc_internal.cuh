@@ -61,6 +61,26 @@ struct vrc_scene {
     size_t h_stage_floats;
 };
 
+// Record grid (query.cu builds it; the renderer reads it): compact record rows and a
+// uniform grid over the unit cube with CSR lists of the records overlapping each cell.
+struct vrc_grid {
+    int n;                 // records
+    int G;                 // cells per axis
+    int order;             // 1 or 2
+    float4* rec;           // [n][4]: (pos, R), (L, g_r.x), (g_r.y, g_r.z, g_g.x, g_g.y), (g_g.z, g_b)
+    float4* hess;          // [n][5]: 18 Hessian entries (order 2), padded
+    int* cell_start;       // [G^3 + 1]
+    int* cell_list;        // [entries]
+    long long entries;
+    // query scratch (grown on demand)
+    int* q_cell;           // [cap]
+    int* q_rank;           // [cap]
+    int* q_perm;           // [cap]
+    int* q_count;          // [G^3 + 1]
+    int* scan_tmp;         // block sums
+    int q_cap;
+};
+
 // ------------------------------------------------------------------ small vector ops
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }

@@ -1,0 +1,92 @@
+"""Adaptive record placement (Sec. 6): add records until every candidate point is covered.
+
+Waves run from coarse to fine grid levels.  In wave `level` every cell of a 2^level grid
+over the unit cube that still holds an uncovered pool candidate (whose own level is at
+most `level`) gets one site -- the candidate with the smallest index (vrc_select_sites);
+full records are computed at the sites (vrc_compute_records), the grid is rebuilt and
+the candidates are queried (vrc_query_inscatter); covered candidates leave the pool
+(vrc_update_coverage).  Candidates still uncovered after the finest wave get a record
+each.  Coverage always uses the full records' radii, so the result honours the error
+tolerance whatever picked the sites.
+
+Plain placement starts every candidate at the coarsest level.  Learned placement first
+predicts each candidate's radius from its coarse ray set (vrc_coarse_features,
+vrc_mlp_predict) and lets it join only at the wave whose cell matches that radius
+(vrc_levels_from_radius): regions of small radius skip the coarse waves, whose records
+would cover almost nothing there.
+
+This module only sequences library calls; all work runs in libvrc's kernels.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+from . import (MLP, Grid, Scene, alloc_records, coarse_features, compute_records, levels_from_radius,
+               query_inscatter, select_sites, update_coverage, _torch)
+
+
+@dataclass
+class PlacementResult:
+    n_records: int
+    waves: list = field(default_factory=list)      # (level, sites) per wave
+    seconds: float = 0.0
+    records: dict = None
+    grid: Grid = None
+    uncovered_after_waves: int = 0
+
+
+def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, mlp: MLP = None,
+          coarse_params=None, cell_over_radius: float = 1.0, capacity: int = None) -> PlacementResult:
+    """Place records until every candidate point `cand` [n,3] (CUDA float32) is covered."""
+    torch = _torch()
+    n = cand.shape[0]
+    cap = capacity or n
+    t0 = time.perf_counter()
+    recs = alloc_records(cap, full=False)
+    level = torch.full((n,), start_level, dtype=torch.int32, device=cand.device)
+    if mlp is not None:
+        feat = coarse_features(scene, cand, coarse_params)
+        logr = mlp.predict(feat)
+        levels_from_radius(logr, level, cell_over_radius, start_level, max_level)
+    fine = min(8, max_level + 1)
+    scratch = torch.empty((8 ** fine + 2 * n + n // 1024 + 2,), dtype=torch.int32, device=cand.device)
+    site_idx = torch.empty((n,), dtype=torch.int32, device=cand.device)
+    site_pts = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
+    count = torch.empty((n,), dtype=torch.int32, device=cand.device)
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
+    total = 0
+    res = PlacementResult(0)
+    grid = None
+
+    def add_records(pts, m):
+        nonlocal total, grid
+        if total + m > cap:
+            raise RuntimeError("placement capacity exceeded")
+        out = {k: v[total:total + m] for k, v in recs.items()}
+        compute_records(scene, pts[:m].contiguous(), params, out=out)
+        total += m
+        view = {k: v[:total] for k, v in recs.items()}
+        grid = Grid(view, n=total)
+        query_inscatter(grid, cand, rgb, count)
+        update_coverage(count, level)
+
+    for lv in range(start_level, max_level + 1):
+        m = select_sites(cand, level, lv, scratch, site_idx, site_pts)
+        res.waves.append((lv, m))
+        if m:
+            add_records(site_pts, m)
+    # candidates still uncovered get sites on the finest grid until none is left (each
+    # wave covers at least its own sites, so this ends)
+    left = select_sites(cand, level, fine, scratch, site_idx, site_pts)
+    res.uncovered_after_waves = left
+    while left:
+        add_records(site_pts, left)
+        res.waves.append((fine, left))
+        left = select_sites(cand, level, fine, scratch, site_idx, site_pts)
+    torch.cuda.synchronize()
+    res.seconds = time.perf_counter() - t0
+    res.n_records = total
+    res.records = {k: v[:total] for k, v in recs.items()}
+    res.grid = grid
+    return res
