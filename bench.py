@@ -394,6 +394,77 @@ def run_batching(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_render(args, w):
+    """Extra measurement (not the default line): one 1920x1080 frame of the render-shaped
+    workload, plain vs learned placement, RMSE against a crop composited from a full record
+    at every march point (those records spot-checked against the FP64 oracle)."""
+    import torch
+    import oracle
+    import oracle.mlp as M
+    import paper_1805_09258_gb300 as vrc
+    from paper_1805_09258_gb300 import build as vbuild, learned
+    from paper_1805_09258_gb300.renderer import render_frame
+    vbuild.build()
+    ex = w.extra
+    rp = w.params
+    coarse = W.RecordParams(n_bands=8, n_bins=16, seed=W.configs.SEED_JITTER + 1000, omega_o=rp.omega_o)
+    scene = vrc.Scene.from_workload(w.scene)
+    cam = vrc.Camera.make(ex["camera"], ex["forward"], ex["vfov_deg"], ex["width"], ex["height"])
+    steps = ex["steps"]
+    # train the predictor on records of 4 render-style scenes (other seeds)
+    t0 = time.perf_counter()
+    exs = learned.ExampleSet(4 * 16384)
+    for seed in (11, 12, 13, 14):
+        wsc = W.configs.render_scene(seed)
+        exs.add(vrc.Scene.from_workload(wsc), W.record_positions(wsc, 16384, seed + 50), rp, coarse)
+    mlp = vrc.MLP(M.init_params(5))
+    F, T = exs.view()
+    learned.train(mlp, F, T, steps=1500, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    out = {}
+    runs = [("learned", mlp, rp.eps)] + [(f"plain_eps{e:g}", None, e) for e in (rp.eps, rp.eps / 2, rp.eps / 4)]
+    for name, net, eps in runs:
+        rpe = W.configs.replace(rp, eps=eps)
+        render_frame(scene, cam, rpe, steps=steps, stride=8, mlp=net, coarse_params=coarse)     # warm-up
+        out[name] = render_frame(scene, cam, rpe, steps=steps, stride=8, mlp=net, coarse_params=coarse)
+    # reference crop: a full record at every march point of the central 64 x 64 pixels
+    cw = 64
+    x0, y0 = ex["width"] // 2 - cw // 2, ex["height"] // 2 - cw // 2
+    pts, valid = vrc.march_points(scene, cam, x0, y0, cw, cw, 1, steps)
+    rp_ref = W.configs.replace(rp, n_bands=32, n_bins=64, seed=W.configs.SEED_JITTER + 7)   # 4x the rays, own jitter
+    full = vrc.compute_records(scene, pts, rp_ref, full=False)
+    ref = vrc.composite(scene, cam, x0, y0, cw, cw, steps, full["L"]).cpu().numpy()
+    # FP64 oracle spot check of reference records
+    idx = np.arange(0, pts.shape[0], pts.shape[0] // 8)[:8]
+    pn = pts.cpu().numpy()[idx]
+    orc = oracle.records(oracle.OracleScene(w.scene), rp_ref, pn, rec_ids=idx, track_margins=1)
+    Lg = full["L"].cpu().numpy()[idx].astype(np.float64)
+    spot = float(np.max(np.abs(Lg - orc["L"]) / (1e-4 * np.abs(orc["L"]) + orc["bud_L"] + 1e-12)))
+    res = {}
+    for name, fr in out.items():
+        img = fr.image.cpu().numpy().reshape(ex["height"], ex["width"], 3)[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3)
+        st = fr.placement.records["status"].cpu().numpy()
+        res[name] = {"frame_ms": fr.seconds * 1e3, "records": fr.n_records, "passes": len(fr.passes),
+                     "rel_rmse_vs_full_records": float(np.sqrt(np.mean((img - ref) ** 2)) / np.mean(np.abs(ref))),
+                     "crop_mean": float(np.mean(img)), "crop_max": float(np.max(img)),
+                     "records_clamped_lo": float(np.mean((st & 2) != 0)), "misses_repaired": fr.misses}
+    n_q = ex["width"] * ex["height"] * steps
+    line = {"metric": METRIC, "value": n_q / (out["learned"].seconds), "unit": "march points/s (whole frame)",
+            "runs": res,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": "f32 (f64 eigen-solve)",
+            "data": "synthetic", "config": {"workload": w.name, "scene_tris": w.scene.n_tris,
+                                            "pixels": ex["width"] * ex["height"], "march_steps": steps,
+                                            "record_rays": rp.n_rays, "prepass_stride": 8},
+            "mlp_training_s": train_s,
+            "reference": "full record (32x64 rays) at every march point of the central 64x64 crop",
+            "oracle_spot_check_max_err_over_tol": spot,
+            "reference_crop_mean": float(np.mean(ref)), "reference_crop_max": float(np.max(ref)),
+            "reference_zero_L_fraction": float(np.mean(np.all(full["L"].cpu().numpy() == 0, axis=1))),
+            "spot_L": orc["L"][:, 1].tolist()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,11 +475,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batching"],
-                    help="mid (the default line) or the batching workload (extra measurement)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render"],
+                    help="mid (the default line), or the batching or render workload (extra measurements)")
     args = ap.parse_args()
     if args.workload == "batching":
         run_batching(args, W.config3())
+        return
+    if args.workload == "render":
+        run_render(args, W.config5())
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

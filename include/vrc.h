@@ -226,6 +226,19 @@ int vrc_march_points(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_
 int vrc_render(vrc_scene* scene, const vrc_grid* grid, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w,
                int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
 
+/* The same for a list of pixels (linear index y * width + x): march points [n_pix*steps][3]
+ * in list order; render writes each listed pixel at its own index of the full-frame
+ * d_img [width*height][3] / d_miss.  Asynchronous. */
+int vrc_march_pixels(vrc_scene* scene, const vrc_camera* cam, const int32_t* d_pix, int32_t n_pix, int32_t steps,
+                     float* d_pts, int32_t* d_valid, void* stream);
+int vrc_render_pixels(vrc_scene* scene, const vrc_grid* grid, const vrc_camera* cam, const int32_t* d_pix,
+                      int32_t n_pix, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
+
+/* Indices i (ascending) with d_flags[i] != 0 into d_idx; their number to *h_count
+ * (synchronous).  d_scratch holds 2 n + n/1024 + 2 ints. */
+int vrc_compact_indices(const int32_t* d_flags, int32_t n, int32_t* d_scratch, int64_t scratch_ints, int32_t* d_idx,
+                        int32_t* h_count, void* stream);
+
 /* Pixel values from caller-given radiance at every march point (d_L [w*h*steps][3], in
  * vrc_march_points order) -- e.g. a full record at every point, the reference image. */
 int vrc_composite(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w, int32_t h,
@@ -238,6 +251,18 @@ int vrc_composite(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_t y
  * d_scratch must hold 8^level + 2 n + n/1024 + 2 ints; level <= 8. */
 int vrc_select_sites(const float* d_pts, const int32_t* d_level, int32_t n, int32_t level, int32_t* d_scratch,
                      int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts, int32_t* h_count, void* stream);
+
+/* Learned levels predicted once per cell: after vrc_select_sites at cell_level (which left
+ * each cell's representative -- smallest candidate index -- in the first 8^cell_level
+ * ints of d_scratch), d_site_logr[j] is the predicted log radius of site j (index
+ * d_site_idx[j]); every pool candidate takes its cell representative's level
+ * (as in vrc_levels_from_radius).  d_rep_level [n] is scratch.  Asynchronous. */
+int vrc_levels_by_cell(const float* d_pts, int32_t n, int32_t cell_level, const int32_t* d_scratch,
+                       const int32_t* d_site_idx, const float* d_site_logr, int32_t n_sites, float cell_over_radius,
+                       int32_t lmin, int32_t lmax, int32_t* d_rep_level, int32_t* d_level, void* stream);
+
+/* d_level[i] = start_level where d_valid[i] != 0, else -1 (not a candidate).  Asynchronous. */
+int vrc_init_levels(const int32_t* d_valid, int32_t n, int32_t start_level, int32_t* d_level, void* stream);
 
 /* d_level[i] = -1 (leaves the candidate pool) where d_count[i] > 0.  Asynchronous. */
 int vrc_update_coverage(const int32_t* d_count, int32_t n, int32_t* d_level, void* stream);

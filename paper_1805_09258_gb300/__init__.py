@@ -89,6 +89,11 @@ def load_library(path: Optional[str] = None):
     L.vrc_composite.argtypes = [P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_select_sites.argtypes = [P, P, I32, I32, P, C.c_int64, P, P, P, P]
     L.vrc_update_coverage.argtypes = [P, I32, P, P]
+    L.vrc_init_levels.argtypes = [P, I32, I32, P, P]
+    L.vrc_march_pixels.argtypes = [P, P, P, I32, I32, P, P, P]
+    L.vrc_render_pixels.argtypes = [P, P, P, P, I32, I32, P, P, P]
+    L.vrc_compact_indices.argtypes = [P, I32, P, C.c_int64, P, P, P]
+    L.vrc_levels_by_cell.argtypes = [P, I32, I32, P, P, P, I32, C.c_float, I32, I32, P, P, P]
     L.vrc_levels_from_radius.argtypes = [P, I32, C.c_float, I32, I32, P, P]
     L.vrc_mlp_create.argtypes = [P, C.POINTER(C.c_void_p)]
     L.vrc_mlp_destroy.argtypes = [P]
@@ -478,6 +483,28 @@ def render(scene: Scene, grid: "Grid", cam: Camera, x0, y0, w, h, steps, img=Non
     return img, miss
 
 
+def march_pixels(scene: Scene, cam: Camera, pix, steps, stream=None):
+    torch = _torch()
+    n = pix.shape[0] * steps
+    pts = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    valid = torch.empty((n,), dtype=torch.int32, device="cuda")
+    _check(load_library().vrc_march_pixels(scene.handle, C.byref(cam), _ptr(pix), pix.shape[0], steps, _ptr(pts),
+                                           _ptr(valid), _stream_ptr(stream)), "vrc_march_pixels")
+    return pts, valid
+
+
+def render_pixels(scene: Scene, grid: "Grid", cam: Camera, pix, steps, img, miss, stream=None):
+    _check(load_library().vrc_render_pixels(scene.handle, grid.handle, C.byref(cam), _ptr(pix), pix.shape[0], steps,
+                                            _ptr(img), _ptr(miss), _stream_ptr(stream)), "vrc_render_pixels")
+
+
+def compact_indices(flags, scratch, out, stream=None) -> int:
+    cnt = C.c_int32(0)
+    _check(load_library().vrc_compact_indices(_ptr(flags), flags.shape[0], _ptr(scratch), scratch.numel(), _ptr(out),
+                                              C.byref(cnt), _stream_ptr(stream)), "vrc_compact_indices")
+    return int(cnt.value)
+
+
 def composite(scene: Scene, cam: Camera, x0, y0, w, h, steps, L, stream=None):
     torch = _torch()
     img = torch.empty((w * h, 3), dtype=torch.float32, device="cuda")
@@ -492,6 +519,18 @@ def select_sites(pts, level, wave_level: int, scratch, site_idx, site_pts, strea
                                            scratch.numel(), _ptr(site_idx), _ptr(site_pts), C.byref(cnt),
                                            _stream_ptr(stream)), "vrc_select_sites")
     return int(cnt.value)
+
+
+def levels_by_cell(pts, cell_level: int, scratch, site_idx, site_logr, n_sites: int, cell_over_radius: float,
+                   lmin: int, lmax: int, rep_level, level, stream=None):
+    _check(load_library().vrc_levels_by_cell(_ptr(pts), pts.shape[0], cell_level, _ptr(scratch), _ptr(site_idx),
+                                             _ptr(site_logr), n_sites, cell_over_radius, lmin, lmax, _ptr(rep_level),
+                                             _ptr(level), _stream_ptr(stream)), "vrc_levels_by_cell")
+
+
+def init_levels(valid, level, start_level: int, stream=None):
+    _check(load_library().vrc_init_levels(_ptr(valid), valid.shape[0], start_level, _ptr(level), _stream_ptr(stream)),
+           "vrc_init_levels")
 
 
 def update_coverage(count, level, stream=None):

@@ -87,6 +87,24 @@ __global__ void k_march_points(DevScene sc, Cam c, int x0, int y0, int w, int h,
     }
 }
 
+__global__ void k_march_pixels(DevScene sc, Cam c, const int* pix, int n_pix, int steps, float* pts, int* valid) {
+    long long total = (long long)n_pix * steps;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int k = (int)(i % steps);
+        int p = pix[i / steps];
+        int px = p % c.W, py = p / c.W;
+        float3 o, d;
+        float s_in, ds;
+        bool ok = pixel_span(sc, c, px, py, steps, o, d, s_in, ds);
+        float3 x = ok ? o + d * (s_in + ((float)k + 0.5f) * ds) : f3(0.f, 0.f, 0.f);
+        pts[3 * i] = x.x;
+        pts[3 * i + 1] = x.y;
+        pts[3 * i + 2] = x.z;
+        valid[i] = ok ? 1 : 0;
+    }
+}
+
 // Eq. radianceTaylor at x from the grid's compact records (order 1)
 struct GridView {
     const float4* rec;
@@ -122,12 +140,21 @@ __device__ __forceinline__ float3 cache_lookup(const GridView& g, float3 x, int&
     return f3(ar * inv, ag * inv, ab * inv);
 }
 
-// one thread per pixel: march, look up, accumulate; misses counted per pixel
+// one thread per pixel: march, look up, accumulate; misses counted per pixel.  With a
+// pixel list, thread i renders pixel pix[i] and writes at that pixel's index.
 __global__ void k_render(DevScene sc, Cam c, GridView g, int x0, int y0, int w, int h, int steps, float* img,
-                         int* miss) {
+                         int* miss, const int* pix, int n_pix) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w * h) return;
-    int px = x0 + i % w, py = y0 + i / w;
+    if (i >= (pix ? n_pix : w * h)) return;
+    int px, py;
+    if (pix) {
+        px = pix[i] % c.W;
+        py = pix[i] / c.W;
+        i = pix[i];
+    } else {
+        px = x0 + i % w;
+        py = y0 + i / w;
+    }
     float3 o, d, acc = f3(0.f, 0.f, 0.f);
     float s_in, ds;
     int nmiss = 0;
@@ -231,9 +258,44 @@ __global__ void k_gather_sites(const float* pts, const int* flag, const int* pos
     out_pts[3 * j + 2] = pts[3 * i + 2];
 }
 
+__global__ void k_nonzero(const int* v, int n, int* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = v[i] != 0 ? 1 : 0;
+}
+
+__global__ void k_scatter_idx(const int* flag, const int* pos, const int* sums, int n, int* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i] + sums[i / 1024]] = i;
+}
+
 __global__ void k_cover(const int* count, int n, int* level) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && count[i] > 0) level[i] = -1;
+}
+
+// every pool candidate takes the level predicted for its cell's representative (the
+// candidate with the smallest index in its cell of the 2^cell_level grid)
+__global__ void k_rep_levels(const float* logr, const int* site_idx, int n_sites, float ratio, int lmin, int lmax,
+                             int* rep_level) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_sites) return;
+    float R = __expf(logr[j]);
+    int l = (int)ceilf(-log2f(fmaxf(ratio * R, 1e-6f)));
+    rep_level[site_idx[j]] = min(lmax, max(lmin, l));
+}
+__global__ void k_cell_levels(const float* pts, int n, int G, const int* cell_min, const int* rep_level, int* level) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || level[i] < 0) return;
+    int ix = min(G - 1, max(0, (int)floorf(pts[3 * i] * G)));
+    int iy = min(G - 1, max(0, (int)floorf(pts[3 * i + 1] * G)));
+    int iz = min(G - 1, max(0, (int)floorf(pts[3 * i + 2] * G)));
+    int rep = cell_min[((size_t)ix * G + iy) * G + iz];
+    if (rep >= 0 && rep < n) level[i] = rep_level[rep];
+}
+
+__global__ void k_init_levels(const int* valid, int n, int start, int* level) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) level[i] = valid[i] ? start : -1;
 }
 
 // learned level of a candidate from its predicted log radius: the finest level whose
@@ -286,7 +348,8 @@ extern "C" int vrc_render(vrc_scene* s, const vrc_grid* grid, const vrc_camera* 
     if (grid->order != 1) return VRC_ERR_INVALID;
     GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G};
     int n = w * h;
-    k_render<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, x0, y0, w, h, steps, d_img, d_miss);
+    k_render<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, x0, y0, w, h, steps, d_img, d_miss,
+                                                                  nullptr, 0);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
@@ -343,4 +406,71 @@ extern "C" int vrc_levels_from_radius(const float* d_logr, int32_t n, float cell
     k_levels_from_logr<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_logr, n, cell_over_radius, lmin, lmax,
                                                                           d_level);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_init_levels(const int32_t* d_valid, int32_t n, int32_t start_level, int32_t* d_level, void* stream) {
+    if (n < 0 || start_level < 0 || (n > 0 && (!d_valid || !d_level))) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    k_init_levels<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_valid, n, start_level, d_level);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_levels_by_cell(const float* d_pts, int32_t n, int32_t cell_level, const int32_t* d_scratch,
+                                  const int32_t* d_site_idx, const float* d_site_logr, int32_t n_sites,
+                                  float cell_over_radius, int32_t lmin, int32_t lmax, int32_t* d_rep_level,
+                                  int32_t* d_level, void* stream) {
+    if (n < 0 || n_sites < 0 || cell_level < 0 || cell_level > 8 || lmin < 0 || lmax < lmin || lmax > 8 ||
+        !(cell_over_radius > 0.f))
+        return VRC_ERR_INVALID;
+    if (n == 0 || n_sites == 0) return VRC_OK;
+    if (!d_pts || !d_scratch || !d_site_idx || !d_site_logr || !d_rep_level || !d_level) return VRC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_rep_levels<<<(n_sites + 255) / 256, 256, 0, st>>>(d_site_logr, d_site_idx, n_sites, cell_over_radius, lmin, lmax,
+                                                        d_rep_level);
+    k_cell_levels<<<(n + 255) / 256, 256, 0, st>>>(d_pts, n, 1 << cell_level, d_scratch, d_rep_level, d_level);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_march_pixels(vrc_scene* s, const vrc_camera* cam, const int32_t* d_pix, int32_t n_pix, int32_t steps,
+                                float* d_pts, int32_t* d_valid, void* stream) {
+    if (!s || !cam || n_pix < 0 || steps < 1) return VRC_ERR_INVALID;
+    if (n_pix == 0) return VRC_OK;
+    if (!d_pix || !d_pts || !d_valid) return VRC_ERR_INVALID;
+    Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
+    long long total = (long long)n_pix * steps;
+    int blocks = (int)std::min<long long>((total + 255) / 256, (long long)s->sm_count * 32);
+    k_march_pixels<<<blocks, 256, 0, (cudaStream_t)stream>>>(s->dev, c, d_pix, n_pix, steps, d_pts, d_valid);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_render_pixels(vrc_scene* s, const vrc_grid* grid, const vrc_camera* cam, const int32_t* d_pix,
+                                 int32_t n_pix, int32_t steps, float* d_img, int32_t* d_miss, void* stream) {
+    if (!s || !grid || !cam || n_pix < 0 || steps < 1 || grid->order != 1) return VRC_ERR_INVALID;
+    if (n_pix == 0) return VRC_OK;
+    if (!d_pix || !d_img) return VRC_ERR_INVALID;
+    Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
+    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G};
+    k_render<<<(n_pix + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, 0, 0, 0, 0, steps, d_img, d_miss,
+                                                                      d_pix, n_pix);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_compact_indices(const int32_t* d_flags, int32_t n, int32_t* d_scratch, int64_t scratch_ints,
+                                   int32_t* d_idx, int32_t* h_count, void* stream) {
+    if (n < 0 || !h_count) return VRC_ERR_INVALID;
+    *h_count = 0;
+    if (n == 0) return VRC_OK;
+    const int nblk = (n + 1023) / 1024;
+    if (!d_flags || !d_scratch || !d_idx || scratch_ints < 2LL * n + nblk + 1) return VRC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* flag = d_scratch;
+    int* pos = flag + n;
+    int* sums = pos + n;
+    k_nonzero<<<(n + 255) / 256, 256, 0, st>>>(d_flags, n, flag);
+    k_flag_scan<<<nblk, 1024, 0, st>>>(flag, n, pos, sums);
+    k_flag_tops<<<1, 32, 0, st>>>(sums, nblk, sums + nblk);
+    k_scatter_idx<<<(n + 255) / 256, 256, 0, st>>>(flag, pos, sums, n, d_idx);
+    VRC_CUDA_CHECK(cudaMemcpyAsync(h_count, sums + nblk, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    VRC_CUDA_CHECK(cudaStreamSynchronize(st));
+    return VRC_OK;
 }

@@ -22,8 +22,8 @@ from __future__ import annotations
 import time
 from dataclasses import dataclass, field
 
-from . import (MLP, Grid, Scene, alloc_records, coarse_features, compute_records, levels_from_radius,
-               query_inscatter, select_sites, update_coverage, _torch)
+from . import (MLP, Grid, Scene, alloc_records, coarse_features, compute_records, init_levels, levels_by_cell,
+               levels_from_radius, query_inscatter, select_sites, update_coverage, _torch)
 
 
 @dataclass
@@ -37,27 +37,49 @@ class PlacementResult:
 
 
 def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, mlp: MLP = None,
-          coarse_params=None, cell_over_radius: float = 1.0, capacity: int = None) -> PlacementResult:
-    """Place records until every candidate point `cand` [n,3] (CUDA float32) is covered."""
+          coarse_params=None, cell_over_radius: float = 1.0, capacity: int = None, valid=None,
+          base: PlacementResult = None, predict_level: int = 5) -> PlacementResult:
+    """Place records until every candidate point `cand` [n,3] (CUDA float32) is covered.
+
+    valid [n] (int32, nullable): only nonzero entries are candidates.  base: an earlier
+    placement whose records are kept (the new records are appended after them).
+    """
     torch = _torch()
     n = cand.shape[0]
-    cap = capacity or n
     t0 = time.perf_counter()
+    prev = 0 if base is None else base.n_records
+    cap = capacity or (prev + n)
     recs = alloc_records(cap, full=False)
-    level = torch.full((n,), start_level, dtype=torch.int32, device=cand.device)
-    if mlp is not None:
-        feat = coarse_features(scene, cand, coarse_params)
-        logr = mlp.predict(feat)
-        levels_from_radius(logr, level, cell_over_radius, start_level, max_level)
+    if prev:
+        for k, v in base.records.items():
+            recs[k][:prev].copy_(v)
+    level = torch.empty((n,), dtype=torch.int32, device=cand.device)
+    if valid is None:
+        level.fill_(start_level)
+    else:
+        init_levels(valid, level, start_level)
     fine = min(8, max_level + 1)
     scratch = torch.empty((8 ** fine + 2 * n + n // 1024 + 2,), dtype=torch.int32, device=cand.device)
     site_idx = torch.empty((n,), dtype=torch.int32, device=cand.device)
     site_pts = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
+    if mlp is not None:
+        # predict once per cell of a 2^predict_level grid (its smallest-index candidate)
+        # and give every candidate of the cell that level
+        m = select_sites(cand, level, predict_level, scratch, site_idx, site_pts)
+        if m:
+            feat = coarse_features(scene, site_pts[:m].contiguous(), coarse_params)
+            logr = mlp.predict(feat)
+            rep = torch.empty((n,), dtype=torch.int32, device=cand.device)
+            levels_by_cell(cand, predict_level, scratch, site_idx, logr, m, cell_over_radius, start_level, max_level,
+                           rep, level)
     count = torch.empty((n,), dtype=torch.int32, device=cand.device)
     rgb = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
-    total = 0
+    total = prev
     res = PlacementResult(0)
-    grid = None
+    grid = base.grid if base is not None else None
+    if grid is not None:
+        query_inscatter(grid, cand, rgb, count)
+        update_coverage(count, level)
 
     def add_records(pts, m):
         nonlocal total, grid

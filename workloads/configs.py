@@ -129,8 +129,13 @@ def config2() -> Workload:
 
 
 def config3() -> Workload:
-    """Batching workload: 100,000 triangles, 100,000 records with 8x16 .. 64x128 rays."""
-    scene = _box_scene("8,333 boxes + ground (100,000 tris)", 8333, 0.01, 0.05, True, 4,
+    """Batching workload: 100,000 triangles, 100,000 records with 8x16 .. 64x128 rays.
+
+    Box sides are log-uniform in [0.005, 0.025]: the boxes' optical depth is about 2.3 per
+    unit length, so a shadow ray to the light is blocked with a probability well below
+    one (sides of 0.01 .. 0.05 would give about 8 per unit length and an almost unlit
+    scene, where every record's radius collapses to r_min)."""
+    scene = _box_scene("8,333 boxes + ground (100,000 tris)", 8333, 0.005, 0.025, True, 4,
                        Medium(0.8, 0.2, 0.5), SEED_SCENE)
     n = 100_000
     return Workload("batching: 100k tris, 100k records, 8x16..64x128 rays", scene,
@@ -147,10 +152,16 @@ def config4(scene_seed: int = SEED_SCENE) -> Workload:
                     extra={"coarse": RecordParams(n_bands=8, n_bins=16, seed=SEED_JITTER + 1000)})
 
 
+def render_scene(seed: int = SEED_SCENE) -> Scene:
+    """20,833 boxes (sides log-uniform in [0.003, 0.016], box optical depth about 2.3 per
+    unit length, as in the batching scene) + ground: 250,000 triangles."""
+    return _box_scene("20,833 boxes + ground (250,000 tris)", 20833, 0.003, 0.016, True, 4,
+                      Medium(0.4, 0.1, 0.7), seed)
+
+
 def config5() -> Workload:
     """Render-shaped workload: 250,000 triangles, 1920x1080 camera, 64 march steps."""
-    scene = _box_scene("20,833 boxes + ground (250,000 tris)", 20833, 0.01, 0.05, True, 4,
-                       Medium(0.4, 0.1, 0.7), SEED_SCENE)
+    scene = render_scene()
     return Workload("render: 250k tris, 1920x1080x64 march points", scene,
                     RecordParams(n_bands=16, n_bins=32, omega_o=(0.0, -1.0, 0.0)),
                     n_records=0, n_queries=1920 * 1080 * 64,
