@@ -396,8 +396,9 @@ def run_batching(args, w):
 
 def run_render(args, w):
     """Extra measurement (not the default line): one 1920x1080 frame of the render-shaped
-    workload, plain vs learned placement, RMSE against a crop composited from a full record
-    at every march point (those records spot-checked against the FP64 oracle)."""
+    workload, plain vs learned placement with spherical or ellipsoidal records, RMSE against
+    a crop composited from a full record at every march point (those records spot-checked
+    against the FP64 oracle)."""
     import torch
     import oracle
     import oracle.mlp as M
@@ -423,11 +424,14 @@ def run_render(args, w):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     out = {}
-    runs = [("learned", mlp, rp.eps)] + [(f"plain_eps{e:g}", None, e) for e in (rp.eps, rp.eps / 2, rp.eps / 4)]
-    for name, net, eps in runs:
+    runs = [("learned", mlp, rp.eps, False), ("learned_aniso", mlp, rp.eps, True)]
+    runs += [(f"plain_eps{e:g}", None, e, False) for e in (rp.eps, rp.eps / 2, rp.eps / 4)]
+    runs += [(f"plain_aniso_eps{e:g}", None, e, True) for e in (rp.eps, rp.eps / 2)]
+    for name, net, eps, aniso in runs:
         rpe = W.configs.replace(rp, eps=eps)
-        render_frame(scene, cam, rpe, steps=steps, stride=8, mlp=net, coarse_params=coarse)     # warm-up
-        out[name] = render_frame(scene, cam, rpe, steps=steps, stride=8, mlp=net, coarse_params=coarse)
+        kw = dict(steps=steps, stride=8, mlp=net, coarse_params=coarse, aniso=aniso)
+        render_frame(scene, cam, rpe, **kw)     # warm-up
+        out[name] = render_frame(scene, cam, rpe, **kw)
     # reference crop: a full record at every march point of the central 64 x 64 pixels
     cw = 64
     x0, y0 = ex["width"] // 2 - cw // 2, ex["height"] // 2 - cw // 2

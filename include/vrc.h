@@ -110,7 +110,13 @@ typedef struct {
  *   n_shells [n]    medium shells K = ceil(max t_end / dt), NULL to skip
  *   log_radius [n]  natural log of the radius (training target of the learned predictor), NULL to skip
  *   hit_prim, hit_t [n][dbg_stride]  per-ray primary hit id (-1 = escaped) and t,
- *                   for rays v < n_bands*n_bins + 2; NULL to skip */
+ *                   for rays v < n_bands*n_bins + 2; NULL to skip
+ *   radii [n][3]    ellipsoidal record (Eq. radiusAniso3D per eigenvalue, Sec. 5): the
+ *                   principal radius along each eigenvector of the luminance Hessian, in
+ *                   the order of eig, clamped to [r_min, r_max]; NULL to skip
+ *   axes [n][9]     the matching unit eigenvectors, row i for eig[i] (FP64 solve, stored
+ *                   as float); NULL to skip.  Eigenvectors of equal eigenvalues are any
+ *                   orthonormal basis of their eigenspace (the ellipsoid is unique). */
 typedef struct {
     float* L;
     float* grad;
@@ -134,6 +140,8 @@ typedef struct {
     int32_t* hit_prim;
     float* hit_t;
     int32_t dbg_stride;
+    float* radii;
+    float* axes;
 } vrc_records_view;
 
 /* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default. */
@@ -196,6 +204,16 @@ typedef struct vrc_grid vrc_grid;
 int vrc_build_record_grid(const vrc_records_view* recs, int32_t n, int32_t extrap_order, vrc_grid** out,
                           void* stream);
 void vrc_destroy_grid(vrc_grid* grid);
+
+/* The same structure for ellipsoidal records (Eq. radiusAniso3D per eigenvalue, Sec. 5;
+ * anisotropic cache points, Sec. 6): record k covers the points with D^T M_k D < 1,
+ * D = x' - x_k, M_k = sum_i v_i v_i^T / R_i^2 from `radii` and `axes` of `recs` (both
+ * required), and vrc_query_inscatter on this grid uses rho = sqrt(D^T M_k D) in place of
+ * |D| / R_k (membership rho < 1, d = 1 - rho).  Cells list every record whose bounding
+ * box and bounding sphere (largest radius) both meet them.  Same ownership, errors and
+ * synchronisation as vrc_build_record_grid. */
+int vrc_build_record_grid_aniso(const vrc_records_view* recs, int32_t n, int32_t extrap_order, vrc_grid** out,
+                                void* stream);
 
 /* Answer nq queries d_q [nq][3] by Eq. radianceTaylor: the weighted first-order (or,
  * with extrap_order 2, second-order) Taylor extrapolation from every record k with

@@ -93,6 +93,8 @@ def lib():
         _lib.orc_cell_vertices.argtypes = [C.c_int, C.c_int, C.c_int, P]
         _lib.orc_trace.argtypes = [P, P, P, C.c_int, P, P, P, P]
         _lib.orc_query.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P, P, P]
+        _lib.orc_query_aniso.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P, P, P]
+        _lib.orc_aniso.argtypes = [C.c_double, P, C.c_double, C.c_double, C.c_double, P, P, P, P]
         _lib.orc_coarse_features.argtypes = [P, P, P, P, C.c_int, P, P]
     return _lib
 
@@ -273,6 +275,44 @@ def radius(LY: float, h6, eps: float, r_min: float, r_max: float):
     return R, int(st[0]), lam
 
 
+LUM = np.array([0.2126, 0.7152, 0.0722])     # Rec.709 luminance weights (R15)
+
+
+def aniso(LY: float, h6, eps: float, r_min: float, r_max: float):
+    """Ellipsoidal record region (R17): (lam[3] ascending, radii[3], axes[3,3] rows =
+    unit eigenvectors, metric[6] upper triangle of M = sum v v^T / R^2, status bits)."""
+    h = _f64(h6)
+    lam, radii, axes, metric = np.zeros(3), np.zeros(3), np.zeros(9), np.zeros(6)
+    st = lib().orc_aniso(LY, _p(h), eps, r_min, r_max, _p(lam), _p(radii), _p(axes), _p(metric))
+    return lam, radii, axes.reshape(3, 3), metric, int(st)
+
+
+def aniso_records(L, hess, eps: float, r_min: float, r_max: float):
+    """aniso() for every record from its RGB radiance L [n,3] and Hessian hess [n,18]:
+    the luminance L_Y = LUM . L and H_Y = sum_c LUM_c H_c.  Returns (radii [n,3],
+    axes [n,3,3], metric [n,6], lam [n,3], status [n])."""
+    L = np.asarray(L, np.float64).reshape(-1, 3)
+    H = np.asarray(hess, np.float64).reshape(-1, 3, 6)
+    n = L.shape[0]
+    radii, axes, metric, lam = np.zeros((n, 3)), np.zeros((n, 3, 3)), np.zeros((n, 6)), np.zeros((n, 3))
+    status = np.zeros(n, np.int32)
+    for k in range(n):
+        LY = float(LUM[0] * L[k, 0] + LUM[1] * L[k, 1] + LUM[2] * L[k, 2])
+        hY = LUM[0] * H[k, 0] + LUM[1] * H[k, 1] + LUM[2] * H[k, 2]
+        lam[k], radii[k], axes[k], metric[k], status[k] = aniso(LY, hY, eps, r_min, r_max)
+    return radii, axes, metric, lam, status
+
+
+def metric_matrix(m6) -> np.ndarray:
+    """[..., 6] upper triangles (xx xy xz yy yz zz) -> [..., 3, 3] symmetric matrices."""
+    m6 = np.asarray(m6, np.float64)
+    M = np.empty(m6.shape[:-1] + (3, 3))
+    for e, (i, j) in enumerate(((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
+        M[..., i, j] = m6[..., e]
+        M[..., j, i] = m6[..., e]
+    return M
+
+
 def ray_directions(rp, rec: int = 0) -> np.ndarray:
     p = make_params(rp)
     out = np.zeros((rp.n_bands * rp.n_bins + 2, 3))
@@ -308,6 +348,21 @@ def query(rec_pos, rec_R, rec_L, rec_grad, rec_hess, q, order: int = 1):
     near = np.zeros(nq, np.int32)
     lib().orc_query(_p(rec_pos), _p(rec_R), _p(rec_L), _p(rec_grad), _p(rec_hess), rec_pos.shape[0], _p(q),
                     nq, order, _p(out), _p(st), _p(near))
+    return out, st, near
+
+
+def query_aniso(rec_pos, rec_metric, rec_L, rec_grad, rec_hess, q, order: int = 1):
+    """Eq. radianceTaylor over ellipsoidal records (R17) by brute force.  Returns
+    (rgb, count, near)."""
+    rec_pos, rec_metric, rec_L, rec_grad = (_f64(a) for a in (rec_pos, rec_metric, rec_L, rec_grad))
+    rec_hess = _f64(rec_hess) if rec_hess is not None else np.zeros((rec_pos.shape[0], 18))
+    q = _f64(q).reshape(-1, 3)
+    nq = q.shape[0]
+    out = np.zeros((nq, 3))
+    st = np.zeros(nq, np.int32)
+    near = np.zeros(nq, np.int32)
+    lib().orc_query_aniso(_p(rec_pos), _p(rec_metric), _p(rec_L), _p(rec_grad), _p(rec_hess), rec_pos.shape[0],
+                          _p(q), nq, order, _p(out), _p(st), _p(near))
     return out, st, near
 
 

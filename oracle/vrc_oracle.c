@@ -49,6 +49,10 @@
  *      Hessian with the MC luminance, clamped to [r_min, r_max].
  *  R16 ray hits: smallest t, then lowest primitive id; t_min = 1e-6; surface
  *      shadow rays start 1e-5 along the normal facing x.
+ *  R17 ellipsoidal records: one radius per Hessian eigenvalue (Eq. radiusAniso3D
+ *      with |lambda_i|, the same clamps) along its eigenvector; a query's distance
+ *      ratio |x' - x_k| / R_k becomes the ellipsoidal norm sqrt(D^T M_k D), with
+ *      M_k = sum_i v_i v_i^T / R_i^2, in the membership test and in d = 1 - ratio.
  */
 #include <math.h>
 #include <pthread.h>
@@ -732,8 +736,10 @@ int orc_cell_vertices(int nb, int ns, int c, int* out3) {
 }
 
 /* ------------------------------------------------ eigenvalues and radius */
-static void jacobi3(const double Hin[3][3], double lam[3]) {
-    double a[3][3];
+/* cyclic Jacobi rotations; lam ascending, V (if not NULL) gets the matching unit
+ * eigenvectors as its columns: H V[:, i] = lam[i] V[:, i] */
+static void jacobi3v(const double Hin[3][3], double lam[3], double V[3][3]) {
+    double a[3][3], U[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     memcpy(a, Hin, sizeof(a));
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
@@ -757,13 +763,26 @@ static void jacobi3(const double Hin[3][3], double lam[3]) {
                     e[q][k] = s * b[p][k] + c * b[q][k];
                 }
                 memcpy(a, e, sizeof(a));
+                for (int k = 0; k < 3; ++k) {          /* U <- U R */
+                    double up = U[k][p], uq = U[k][q];
+                    U[k][p] = c * up - s * uq;
+                    U[k][q] = s * up + c * uq;
+                }
             }
     }
-    lam[0] = a[0][0]; lam[1] = a[1][1]; lam[2] = a[2][2];
+    int idx[3] = {0, 1, 2};
+    double d[3] = {a[0][0], a[1][1], a[2][2]};
     for (int i = 0; i < 2; ++i)                        /* ascending */
         for (int j = 0; j < 2 - i; ++j)
-            if (lam[j] > lam[j + 1]) { double t = lam[j]; lam[j] = lam[j + 1]; lam[j + 1] = t; }
+            if (d[idx[j]] > d[idx[j + 1]]) { int t = idx[j]; idx[j] = idx[j + 1]; idx[j + 1] = t; }
+    for (int i = 0; i < 3; ++i) {
+        lam[i] = d[idx[i]];
+        if (V)
+            for (int k = 0; k < 3; ++k) V[k][i] = U[k][idx[i]];
+    }
 }
+
+static void jacobi3(const double Hin[3][3], double lam[3]) { jacobi3v(Hin, lam, NULL); }
 
 void orc_eig3(const double* h6, double* lam) {
     double H[3][3] = {{h6[0], h6[1], h6[2]}, {h6[1], h6[3], h6[4]}, {h6[2], h6[4], h6[5]}};
@@ -784,6 +803,43 @@ double orc_radius(double LY, const double* h6, double eps, double r_min, double 
 }
 
 static const double LUM[3] = {0.2126, 0.7152, 0.0722};   /* Rec.709 luminance */
+
+/* Ellipsoidal records (Eq. radiusAniso3D per eigenvalue, Sec. 5 and supplemental S.11):
+ * principal radius R_i = (15 L_Y eps / (4 pi |lambda_i|))^(1/5) along the eigenvector v_i
+ * of the luminance Hessian, clamped to [r_min, r_max] like the isotropic radius (L_Y <= 0
+ * or non-finite: r_min on every axis; lambda_i = 0: r_max on that axis).  Outputs:
+ * lam[3] ascending, radii[3] in that order, axes[9] row i = v_i, metric[6] = the
+ * symmetric M = sum_i v_i v_i^T / R_i^2 (upper triangle xx xy xz yy yz zz), so that the
+ * record's region is D^T M D < 1. */
+int orc_aniso(double LY, const double* h6, double eps, double r_min, double r_max, double* lam, double* radii,
+              double* axes, double* metric) {
+    double H[3][3] = {{h6[0], h6[1], h6[2]}, {h6[1], h6[3], h6[4]}, {h6[2], h6[4], h6[5]}};
+    double V[3][3];
+    jacobi3v(H, lam, V);
+    int status = 0;
+    int bad = !isfinite(LY) || !isfinite(lam[0]) || !isfinite(lam[1]) || !isfinite(lam[2]);
+    for (int i = 0; i < 3; ++i) {
+        double R;
+        double al = fabs(lam[i]);
+        if (bad) { status |= REC_NONFINITE | REC_CLAMP_LO; R = r_min; }
+        else if (!(LY > 0)) { status |= REC_CLAMP_LO; R = r_min; }
+        else if (al == 0.0) { status |= REC_CLAMP_HI; R = r_max; }
+        else {
+            R = pow(15.0 * LY * eps / (4.0 * ORC_PI * al), 0.2);
+            if (R < r_min) { status |= REC_CLAMP_LO; R = r_min; }
+            if (R > r_max) { status |= REC_CLAMP_HI; R = r_max; }
+        }
+        radii[i] = R;
+        for (int k = 0; k < 3; ++k) axes[3 * i + k] = V[k][i];
+    }
+    static const int IJ[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int e = 0; e < 6; ++e) {
+        double m = 0.0;
+        for (int i = 0; i < 3; ++i) m += V[IJ[e][0]][i] * V[IJ[e][1]][i] / (radii[i] * radii[i]);
+        metric[e] = m;
+    }
+    return status;
+}
 
 /* ---------------------------------------------------- one record (Secs. 4-5) */
 typedef struct {
@@ -1376,6 +1432,48 @@ int orc_query(const double* rpos, const double* rR, const double* rL, const doub
             if (fabs(dist - R) <= 1e-5 * R) nr = 1;
             if (!(dist < R)) continue;
             double dd = 1.0 - dist / R;
+            double w = 3.0 * dd * dd - 2.0 * dd * dd * dd;
+            for (int c = 0; c < 3; ++c) {
+                const double* g = &rgrad[9 * k + 3 * c];
+                double val = rL[3 * k + c] + g[0] * D.x + g[1] * D.y + g[2] * D.z;
+                if (order == 2) {
+                    const double* h = &rhess[18 * k + 6 * c];
+                    double quad = h[0] * D.x * D.x + h[3] * D.y * D.y + h[5] * D.z * D.z +
+                                  2.0 * (h[1] * D.x * D.y + h[2] * D.x * D.z + h[4] * D.y * D.z);
+                    val += 0.5 * quad;
+                }
+                acc[c] += w * val;
+            }
+            sw += w;
+            ++cnt;
+        }
+        for (int c = 0; c < 3; ++c) out[3 * i + c] = cnt ? acc[c] / sw : 0.0;
+        status[i] = cnt;
+        if (near) near[i] = nr;
+    }
+    return 0;
+}
+
+/* Eq. radianceTaylor over ellipsoidal records: the distance ratio |D|/R_k becomes the
+ * ellipsoidal norm rho = sqrt(D^T M_k D) (M_k from orc_aniso), C = {k : rho < 1},
+ * d = 1 - rho, w = 3d^2 - 2d^3; with M_k = I / R_k^2 this is orc_query.  near[q] = 1 when
+ * some rho is within 1e-5 of 1.  metric [n_rec][6] upper triangles. */
+int orc_query_aniso(const double* rpos, const double* metric, const double* rL, const double* rgrad,
+                    const double* rhess, int n_rec, const double* q, int nq, int order, double* out,
+                    int32_t* status, int32_t* near) {
+    for (int i = 0; i < nq; ++i) {
+        v3 xq = mk(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+        double acc[3] = {0, 0, 0}, sw = 0.0;
+        int cnt = 0, nr = 0;
+        for (int k = 0; k < n_rec; ++k) {
+            v3 D = sub(xq, mk(rpos[3 * k], rpos[3 * k + 1], rpos[3 * k + 2]));
+            const double* m = &metric[6 * k];
+            double r2 = m[0] * D.x * D.x + m[3] * D.y * D.y + m[5] * D.z * D.z +
+                        2.0 * (m[1] * D.x * D.y + m[2] * D.x * D.z + m[4] * D.y * D.z);
+            double rho = sqrt(fmax(r2, 0.0));
+            if (fabs(rho - 1.0) <= 1e-5) nr = 1;
+            if (!(rho < 1.0)) continue;
+            double dd = 1.0 - rho;
             double w = 3.0 * dd * dd - 2.0 * dd * dd * dd;
             for (int c = 0; c < 3; ++c) {
                 const double* g = &rgrad[9 * k + 3 * c];

@@ -45,7 +45,8 @@ class RecordParamsC(C.Structure):
 class RecordsView(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms",
                                            "hess_ms", "L_ff", "radius", "eig", "kappa", "status", "pos",
-                                           "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t")] + [("dbg_stride", C.c_int32)]
+                                           "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t")] + [("dbg_stride", C.c_int32)] + \
+        [("radii", C.c_void_p), ("axes", C.c_void_p)]
 
 
 class RecordTuning(C.Structure):
@@ -79,6 +80,7 @@ def load_library(path: Optional[str] = None):
     L.vrc_graph_destroy.restype = None
     L.vrc_get_record_tuning.argtypes = [P, P]
     L.vrc_build_record_grid.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
+    L.vrc_build_record_grid_aniso.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
     L.vrc_destroy_grid.argtypes = [P]
     L.vrc_destroy_grid.restype = None
     L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
@@ -200,14 +202,18 @@ RECORD_FIELDS = dict(L=3, grad=9, hess=18, L_ss=3, grad_ss=9, hess_ss=18, L_ms=3
                      L_ff=3, radius=1, eig=3, kappa=1, pos=3)
 
 
-def alloc_records(n: int, full: bool = True, device="cuda"):
-    """Allocate the per-record output tensors (float32; status int32)."""
+def alloc_records(n: int, full: bool = True, device="cuda", aniso: bool = False):
+    """Allocate the per-record output tensors (float32; status int32).  aniso (or full)
+    adds the ellipsoid outputs radii [n,3] and axes [n,9]."""
     torch = _torch()
     out = {}
     for k, w in RECORD_FIELDS.items():
         if not full and k not in ("L", "grad", "hess", "radius", "pos"):
             continue
         out[k] = torch.empty((n, w) if w > 1 else (n,), dtype=torch.float32, device=device)
+    if full or aniso:
+        out["radii"] = torch.empty((n, 3), dtype=torch.float32, device=device)
+        out["axes"] = torch.empty((n, 9), dtype=torch.float32, device=device)
     out["status"] = torch.empty((n,), dtype=torch.int32, device=device)
     if full:
         out["n_cells"] = torch.empty((n,), dtype=torch.int32, device=device)
@@ -219,7 +225,8 @@ def alloc_records(n: int, full: bool = True, device="cuda"):
 def records_view(out: dict, dbg_stride: int = 0) -> RecordsView:
     v = RecordsView()
     for k in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms", "hess_ms", "L_ff", "radius",
-              "eig", "kappa", "status", "pos", "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t"):
+              "eig", "kappa", "status", "pos", "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t",
+              "radii", "axes"):
         setattr(v, k, _ptr(out.get(k)))
     v.dbg_stride = dbg_stride
     return v
@@ -304,18 +311,22 @@ def compute_records_host(scene: Scene, pos: np.ndarray, params) -> dict:
 
 
 class Grid:
-    """Record lookup structure (vrc_build_record_grid / vrc_destroy_grid)."""
+    """Record lookup structure (vrc_build_record_grid / vrc_build_record_grid_aniso /
+    vrc_destroy_grid).  aniso=True uses the records' ellipsoids (radii, axes)."""
 
-    def __init__(self, records: dict, n: Optional[int] = None, extrap_order: int = 1, stream=None):
+    def __init__(self, records: dict, n: Optional[int] = None, extrap_order: int = 1, stream=None,
+                 aniso: bool = False):
         n = records["L"].shape[0] if n is None else n
         v = records_view(records)
         h = C.c_void_p()
         self._keep = records
-        rc = load_library().vrc_build_record_grid(C.byref(v), n, extrap_order, C.byref(h), _stream_ptr(stream))
-        _check(rc, "vrc_build_record_grid")
+        fn = "vrc_build_record_grid_aniso" if aniso else "vrc_build_record_grid"
+        rc = getattr(load_library(), fn)(C.byref(v), n, extrap_order, C.byref(h), _stream_ptr(stream))
+        _check(rc, fn)
         self.handle = h
         self.n = n
         self.extrap_order = extrap_order
+        self.aniso = aniso
 
     def __del__(self):
         try:

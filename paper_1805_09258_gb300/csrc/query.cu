@@ -8,6 +8,10 @@
 // cell, so a query reads exactly one list.  Queries are first binned by cell (count,
 // scan, scatter) so the threads of a warp share one list: its record rows are read as
 // warp-wide broadcasts from L1.  Every buffer is owned by the vrc_grid object.
+//
+// Ellipsoidal records (Eq. radiusAniso3D per eigenvalue): the distance ratio |D| / R_k
+// becomes rho = sqrt(D^T M_k D) with M_k = sum_i v_i v_i^T / R_i^2; a record is listed in
+// the cells that meet both its bounding box and its bounding sphere.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -24,7 +28,7 @@ __global__ void k_pack(const vrc_records_view v, int n, int order, float4* rec, 
     const float* p = v.pos + 3 * k;
     const float* L = v.L + 3 * k;
     const float* g = v.grad + 9 * k;
-    rec[4 * k] = make_float4(p[0], p[1], p[2], v.radius[k]);
+    rec[4 * k] = make_float4(p[0], p[1], p[2], v.radius ? v.radius[k] : 0.f);
     rec[4 * k + 1] = make_float4(L[0], L[1], L[2], g[0]);
     rec[4 * k + 2] = make_float4(g[1], g[2], g[3], g[4]);
     rec[4 * k + 3] = make_float4(g[5], g[6], g[7], g[8]);
@@ -36,6 +40,34 @@ __global__ void k_pack(const vrc_records_view v, int n, int order, float4* rec, 
     }
 }
 
+// ellipsoidal records: M = sum_i v_i v_i^T / R_i^2, bounding-box half extents
+// e_j = sqrt(sum_i R_i^2 v_ij^2), largest radius in rec .w
+__global__ void k_pack_ellipsoid(const vrc_records_view v, int n, float4* rec, float4* ell, float4* ext) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float* r = v.radii + 3 * k;
+    const float* ax = v.axes + 9 * k;
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e2[3] = {0.f, 0.f, 0.f};
+    float rmax = 0.f;
+    for (int i = 0; i < 3; ++i) {
+        const float* u = ax + 3 * i;
+        float inv = 1.0f / (r[i] * r[i]);
+        m[0] = fmaf(u[0] * u[0], inv, m[0]);
+        m[1] = fmaf(u[0] * u[1], inv, m[1]);
+        m[2] = fmaf(u[0] * u[2], inv, m[2]);
+        m[3] = fmaf(u[1] * u[1], inv, m[3]);
+        m[4] = fmaf(u[1] * u[2], inv, m[4]);
+        m[5] = fmaf(u[2] * u[2], inv, m[5]);
+        for (int j = 0; j < 3; ++j) e2[j] = fmaf(r[i] * r[i], u[j] * u[j], e2[j]);
+        rmax = fmaxf(rmax, r[i]);
+    }
+    rec[4 * k].w = rmax;
+    ell[2 * k] = make_float4(m[0], m[1], m[2], m[3]);
+    ell[2 * k + 1] = make_float4(m[4], m[5], 0.f, 0.f);
+    // the box may not exceed the bounding sphere (float rounding of the axes)
+    ext[k] = make_float4(fminf(sqrtf(e2[0]), rmax), fminf(sqrtf(e2[1]), rmax), fminf(sqrtf(e2[2]), rmax), rmax);
+}
+
 __device__ __forceinline__ bool sphere_meets_cell(float3 c, float R, int ix, int iy, int iz, float h) {
     float lx = ix * h, ly = iy * h, lz = iz * h;
     float dx = fmaxf(fmaxf(lx - c.x, c.x - (lx + h)), 0.f);
@@ -44,18 +76,25 @@ __device__ __forceinline__ bool sphere_meets_cell(float3 c, float R, int ix, int
     return dx * dx + dy * dy + dz * dz < R * R;
 }
 
-// PASS 0: count (fill = false) or fill (fill = true) the cells each record's sphere overlaps
+// count (fill = false) or fill (fill = true) the cells each record's sphere overlaps;
+// with `ext` (ellipsoidal records) only the cells within its bounding box
 template <bool FILL>
-__global__ void k_insert(const float4* rec, int n, int G, int* counts, const int* start, int* list) {
+__global__ void k_insert(const float4* rec, const float4* ext, int n, int G, int* counts, const int* start,
+                         int* list) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     float4 a = rec[4 * k];
     float3 c = make_float3(a.x, a.y, a.z);
     float R = a.w;
+    float ex = R, ey = R, ez = R;
+    if (ext) {
+        float4 e = ext[k];
+        ex = e.x, ey = e.y, ez = e.z;
+    }
     float h = 1.0f / G;
-    int x0 = max(0, (int)floorf((c.x - R) * G)), x1 = min(G - 1, (int)floorf((c.x + R) * G));
-    int y0 = max(0, (int)floorf((c.y - R) * G)), y1 = min(G - 1, (int)floorf((c.y + R) * G));
-    int z0 = max(0, (int)floorf((c.z - R) * G)), z1 = min(G - 1, (int)floorf((c.z + R) * G));
+    int x0 = max(0, (int)floorf((c.x - ex) * G)), x1 = min(G - 1, (int)floorf((c.x + ex) * G));
+    int y0 = max(0, (int)floorf((c.y - ey) * G)), y1 = min(G - 1, (int)floorf((c.y + ey) * G));
+    int z0 = max(0, (int)floorf((c.z - ez) * G)), z1 = min(G - 1, (int)floorf((c.z + ez) * G));
     for (int ix = x0; ix <= x1; ++ix)
         for (int iy = y0; iy <= y1; ++iy)
             for (int iz = z0; iz <= z1; ++iz) {
@@ -161,8 +200,9 @@ __global__ void k_scatter_queries(const int* qcell, const int* qrank, const int*
 }
 
 // one thread per query, in cell order
-template <int ORDER>
+template <int ORDER, bool ANISO>
 __global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, const float4* __restrict__ hess,
+                                               const float4* __restrict__ ell,
                                                const int* __restrict__ cell_start, const int* __restrict__ list,
                                                int G, const float* __restrict__ q, const int* __restrict__ perm,
                                                int nq, float* __restrict__ rgb, int* __restrict__ status) {
@@ -180,8 +220,17 @@ __global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, c
         float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
         float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (!(d2 < a.w * a.w)) continue;
+        float dd;
+        if (ANISO) {
+            float4 m0 = __ldg(&ell[2 * k]), m1 = __ldg(&ell[2 * k + 1]);
+            float r2e = fmaf(m0.x * dx, dx, fmaf(m0.w * dy, dy, m1.y * dz * dz)) +
+                        2.0f * fmaf(m0.y * dx, dy, fmaf(m0.z * dx, dz, m1.x * dy * dz));
+            if (!(r2e < 1.0f)) continue;
+            dd = 1.0f - sqrtf(fmaxf(r2e, 0.f));
+        } else {
+            dd = 1.0f - sqrtf(d2) / a.w;
+        }
         float4 r1 = __ldg(&rec[4 * k + 1]), r2 = __ldg(&rec[4 * k + 2]), r3 = __ldg(&rec[4 * k + 3]);
-        float dd = 1.0f - sqrtf(d2) / a.w;
         float w = dd * dd * fmaf(-2.0f, dd, 3.0f);
         float vr = r1.x + fmaf(r1.w, dx, fmaf(r2.x, dy, r2.y * dz));
         float vg = r1.y + fmaf(r2.z, dx, fmaf(r2.w, dy, r3.x * dz));
@@ -230,6 +279,8 @@ extern "C" void vrc_destroy_grid(vrc_grid* g) {
     if (!g) return;
     cudaFree(g->rec);
     cudaFree(g->hess);
+    cudaFree(g->ell);
+    cudaFree(g->ext);
     cudaFree(g->cell_start);
     cudaFree(g->cell_list);
     cudaFree(g->q_cell);
@@ -240,23 +291,32 @@ extern "C" void vrc_destroy_grid(vrc_grid* g) {
     delete g;
 }
 
-extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32_t order, vrc_grid** out,
-                                     void* stream) {
+namespace {
+
+int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, vrc_grid** out, void* stream) {
     if (!v || !out || n < 0 || (order != 1 && order != 2)) return VRC_ERR_INVALID;
-    if (n > 0 && (!v->pos || !v->radius || !v->L || !v->grad || (order == 2 && !v->hess))) return VRC_ERR_INVALID;
+    if (n > 0 && (!v->pos || !v->L || !v->grad || (order == 2 && !v->hess))) return VRC_ERR_INVALID;
+    if (n > 0 && (aniso ? (!v->radii || !v->axes) : !v->radius)) return VRC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     *out = nullptr;
     vrc_grid* g = new vrc_grid();
     g->n = n;
     g->order = order;
-    // cell size: about a quarter of the median radius, at most 64 cells per axis
+    g->aniso = aniso ? 1 : 0;
+    // cell size: about a quarter of the median radius (ellipsoids: of the geometric mean
+    // of the principal radii), at most 64 cells per axis
     int G = 1;
     if (n > 0) {
-        std::vector<float> R(n);
-        if (cudaMemcpyAsync(R.data(), v->radius, sizeof(float) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        std::vector<float> R(aniso ? 3 * (size_t)n : (size_t)n);
+        if (cudaMemcpyAsync(R.data(), aniso ? v->radii : v->radius, sizeof(float) * R.size(), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             vrc_destroy_grid(g);
             return VRC_ERR_CUDA;
+        }
+        if (aniso) {
+            for (int k = 0; k < n; ++k) R[k] = std::cbrt(R[3 * k] * R[3 * k + 1] * R[3 * k + 2]);
+            R.resize(n);
         }
         std::nth_element(R.begin(), R.begin() + n / 2, R.end());
         float med = R[n / 2];
@@ -269,6 +329,7 @@ extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32
     int nblk = (ncell + 1 + SCAN_BLOCK - 1) / SCAN_BLOCK;
     int rc = VRC_OK;
     if ((rc = dev_alloc(&g->rec, 4 * (size_t)n)) || (rc = dev_alloc(&g->hess, order == 2 ? 5 * (size_t)n : 1)) ||
+        (aniso && ((rc = dev_alloc(&g->ell, 2 * (size_t)n)) || (rc = dev_alloc(&g->ext, (size_t)n)))) ||
         (rc = dev_alloc(&g->cell_start, (size_t)ncell + 1)) || (rc = dev_alloc(&g->q_count, (size_t)ncell + 1)) ||
         (rc = dev_alloc(&g->scan_tmp, (size_t)nblk + 1))) {
         vrc_destroy_grid(g);
@@ -277,8 +338,9 @@ extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32
     if (n > 0) {
         int tb = 256, nbk = (n + tb - 1) / tb;
         k_pack<<<nbk, tb, 0, st>>>(*v, n, order, g->rec, g->hess);
+        if (aniso) k_pack_ellipsoid<<<nbk, tb, 0, st>>>(*v, n, g->rec, g->ell, g->ext);
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
-        k_insert<false><<<nbk, tb, 0, st>>>(g->rec, n, G, g->q_count, nullptr, nullptr);
+        k_insert<false><<<nbk, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, nullptr, nullptr);
         exclusive_scan(g->q_count, ncell, g->cell_start, g->scan_tmp, st);
         int total = 0;
         if (cudaMemcpyAsync(&total, g->cell_start + ncell, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -292,7 +354,7 @@ extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32
             return rc;
         }
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
-        k_insert<true><<<nbk, tb, 0, st>>>(g->rec, n, G, g->q_count, g->cell_start, g->cell_list);
+        k_insert<true><<<nbk, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, g->cell_start, g->cell_list);
         k_sort_lists<<<ncell, 256, 0, st>>>(g->cell_start, ncell, g->cell_list);
     } else {
         cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);
@@ -307,6 +369,18 @@ extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32
     }
     *out = g;
     return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32_t order, vrc_grid** out,
+                                     void* stream) {
+    return build_grid(v, n, order, false, out, stream);
+}
+
+extern "C" int vrc_build_record_grid_aniso(const vrc_records_view* v, int32_t n, int32_t order, vrc_grid** out,
+                                           void* stream) {
+    return build_grid(v, n, order, true, out, stream);
 }
 
 extern "C" int vrc_query_inscatter(const vrc_grid* gc, const float* d_q, int32_t nq, float* d_rgb,
@@ -333,11 +407,9 @@ extern "C" int vrc_query_inscatter(const vrc_grid* gc, const float* d_q, int32_t
     int rc = exclusive_scan(g->q_count, ncell, g->q_count, g->scan_tmp, st);
     if (rc) return rc;
     k_scatter_queries<<<nbk, tb, 0, st>>>(g->q_cell, g->q_rank, g->q_count, nq, g->q_perm);
-    if (g->order == 2)
-        k_query<2><<<nbk, tb, 0, st>>>(g->rec, g->hess, g->cell_start, g->cell_list, G, d_q, g->q_perm, nq, d_rgb,
-                                       d_status);
-    else
-        k_query<1><<<nbk, tb, 0, st>>>(g->rec, g->hess, g->cell_start, g->cell_list, G, d_q, g->q_perm, nq, d_rgb,
-                                       d_status);
+    auto kfn = g->order == 2 ? (g->aniso ? k_query<2, true> : k_query<2, false>)
+                             : (g->aniso ? k_query<1, true> : k_query<1, false>);
+    kfn<<<nbk, tb, 0, st>>>(g->rec, g->hess, g->ell, g->cell_start, g->cell_list, G, d_q, g->q_perm, nq, d_rgb,
+                            d_status);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }

@@ -291,9 +291,100 @@ __device__ void eig3_sym(const double h[6], double lam[3]) {
     if (lam[1] < lam[0]) { double tt = lam[0]; lam[0] = lam[1]; lam[1] = tt; }
 }
 
+// ----------------------------------------------------------------- FP64 eigenvectors
+// Unit vector spanning the null space of the symmetric A - l I: the longest cross product
+// of two of its rows (for a simple eigenvalue the rows span the plane orthogonal to the
+// eigenvector).  false when every cross product vanishes (A = l I).
+__device__ bool null_direction(const double h[6], double l, double v[3]) {
+    const double r[3][3] = {{h[0] - l, h[1], h[2]}, {h[1], h[3] - l, h[4]}, {h[2], h[4], h[5] - l}};
+    double best = 0.0;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const double* u = r[p == 2 ? 1 : 0];
+        const double* w = r[p == 0 ? 1 : 2];
+        double c[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        double n2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        if (n2 > best) {
+            best = n2;
+            v[0] = c[0]; v[1] = c[1]; v[2] = c[2];
+        }
+    }
+    if (!(best > 0.0) || !isfinite(best)) return false;
+    double s = 1.0 / sqrt(best);
+    v[0] *= s; v[1] *= s; v[2] *= s;
+    return true;
+}
+
+// Eigenvectors for the ascending eigenvalues lam (rows of V).  The eigenvalue farther from
+// the middle one is isolated first by null_direction; the other two come from the 2x2
+// restriction of A to the orthogonal plane, diagonalised by one plane rotation.
+__device__ void eigvec3_sym(const double h[6], const double lam[3], double V[3][3]) {
+    int first = (lam[2] - lam[1] >= lam[1] - lam[0]) ? 2 : 0;
+    double v[3];
+    if (!null_direction(h, lam[first], v)) {
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) V[i][k] = i == k ? 1.0 : 0.0;
+        return;
+    }
+    // orthonormal (u, w) spanning the plane orthogonal to v
+    int m = fabs(v[0]) <= fabs(v[1]) ? (fabs(v[0]) <= fabs(v[2]) ? 0 : 2) : (fabs(v[1]) <= fabs(v[2]) ? 1 : 2);
+    double e[3] = {m == 0 ? 1.0 : 0.0, m == 1 ? 1.0 : 0.0, m == 2 ? 1.0 : 0.0};
+    double u[3] = {v[1] * e[2] - v[2] * e[1], v[2] * e[0] - v[0] * e[2], v[0] * e[1] - v[1] * e[0]};
+    double un = 1.0 / sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    u[0] *= un; u[1] *= un; u[2] *= un;
+    double w[3] = {v[1] * u[2] - v[2] * u[1], v[2] * u[0] - v[0] * u[2], v[0] * u[1] - v[1] * u[0]};
+    double Au[3] = {h[0] * u[0] + h[1] * u[1] + h[2] * u[2], h[1] * u[0] + h[3] * u[1] + h[4] * u[2],
+                    h[2] * u[0] + h[4] * u[1] + h[5] * u[2]};
+    double Aw[3] = {h[0] * w[0] + h[1] * w[1] + h[2] * w[2], h[1] * w[0] + h[3] * w[1] + h[4] * w[2],
+                    h[2] * w[0] + h[4] * w[1] + h[5] * w[2]};
+    double a = u[0] * Au[0] + u[1] * Au[1] + u[2] * Au[2];
+    double b = u[0] * Aw[0] + u[1] * Aw[1] + u[2] * Aw[2];
+    double c = w[0] * Aw[0] + w[1] * Aw[1] + w[2] * Aw[2];
+    // (cos t, sin t) in the (u, w) frame is the eigenvector of the larger eigenvalue of
+    // [[a, b], [b, c]] for t = atan2(2b, a - c) / 2
+    double t = 0.5 * atan2(2.0 * b, a - c);
+    double cs = cos(t), sn = sin(t);
+    int hi = first == 2 ? 1 : 2, lo = first == 2 ? 0 : 1;
+    for (int k = 0; k < 3; ++k) {
+        V[first][k] = v[k];
+        V[hi][k] = cs * u[k] + sn * w[k];
+        V[lo][k] = -sn * u[k] + cs * w[k];
+    }
+}
+
+// Ellipsoidal record (Eq. radiusAniso3D per eigenvalue): principal radii along the
+// luminance Hessian's eigenvectors, with the clamps of the isotropic radius.
+__device__ __noinline__ void write_ellipsoid(const double h[6], const double lam[3], double LY, bool bad, double eps,
+                                             double r_min, double r_max, float* radii, float* axes) {
+    double V[3][3];
+    if (bad) {
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) V[i][k] = i == k ? 1.0 : 0.0;
+    } else {
+        eigvec3_sym(h, lam, V);
+    }
+    for (int i = 0; i < 3; ++i) {
+        double al = fabs(lam[i]), R;
+        if (bad) R = r_min;
+        else if (!(LY > 0.0)) R = r_min;
+        else if (al == 0.0) R = r_max;
+        else R = fmin(r_max, fmax(r_min, pow(15.0 * LY * eps / (4.0 * 3.14159265358979323846 * al), 0.2)));
+        if (radii) radii[i] = (float)R;
+        if (axes)
+            for (int k = 0; k < 3; ++k) axes[3 * i + k] = (float)V[i][k];
+    }
+}
+
 // ----------------------------------------------------------------- the kernel
+// Registers are capped at 128 per thread (2 blocks of 256 per SM): the traversal phases
+// are latency-bound and need the warps; a lower cap (85) spills the cell math and was
+// slower, an uncapped build took more registers and left one block per SM.
+#ifndef VRC_RECORDS_REGS
+#define VRC_RECORDS_REGS 128
+#endif
+
 template <int NT>
-__global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
+__global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records(DevScene sc, RecArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ float4 smem4[];
     float4* ray = smem4;                                     // (d, t_end) per chunk vertex
@@ -305,6 +396,8 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
     float* tot = mcs + NW * 12;                              // [128]
     int* misc = reinterpret_cast<int*>(tot + 128);           // [4]
     int* wq = misc + 4;                                      // [NW][64] lit-cell queues
+    const int LW = (a.cap + 31) >> 5;
+    unsigned* litm = reinterpret_cast<unsigned*>(wq + NW * 64);   // [2][LW]: vertex has radiance (bit per vertex)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float sigma_t = sc.sigma_t, g = sc.g;
     __shared__ int s_rec;
@@ -340,7 +433,11 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
             __syncthreads();
             // ---------------- primary phase
             float tmax_loc = 0.f;
-            for (int lv = tid; lv < nvert; lv += NT) {
+            const int nvround = (nvert + 31) & ~31;
+            for (int vb = warp * 32; vb < nvround; vb += NT) {
+                const int lv = vb + lane;
+                bool lit_v = false;
+                if (lv < nvert) {
                 int gv, row = 0;
                 bool pole = lv >= rows * ns;
                 if (!pole) {
@@ -364,6 +461,7 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                 Lr[lv] = Lo.x;
                 Lg[lv] = Lo.y;
                 Lb[lv] = Lo.z;
+                lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
                 tmax_loc = fmaxf(tmax_loc, te);
                 bool owned = !pole && row < r1;
                 if (owned && prim >= 0) {
@@ -377,6 +475,9 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                     a.out.hit_prim[o] = prim;
                     a.out.hit_t[o] = te;
                 }
+            }
+                unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
+                if (lane == 0) litm[vb >> 5] = lmk;
             }
             atomicMax(&misc[0], __float_as_int(tmax_loc));   // non-negative floats order as ints
             __syncthreads();
@@ -397,7 +498,12 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                     // ---------------- vertex phase of medium shell k + 1
                     const float tn = ((float)(k + 1) - 0.5f) * a.dt;
                     float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
-                    for (int lv = tid; lv < nvert; lv += NT) {
+                    unsigned* litn = litm + ((k + 1) & 1) * LW;
+                    const int nvround = (nvert + 31) & ~31;
+                    for (int vb = warp * 32; vb < nvround; vb += NT) {
+                        const int lv = vb + lane;
+                        bool lit_v = false;
+                        if (lv < nvert) {
                         float4 rv = ray[lv];
                         float3 d = f3(rv.x, rv.y, rv.z);
                         float3 Lo = f3(0.f, 0.f, 0.f);
@@ -415,6 +521,10 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                         Lrn[lv] = Lo.x;
                         Lrn[a.cap + lv] = Lo.y;
                         Lrn[2 * a.cap + lv] = Lo.z;
+                        lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
+                        }
+                        unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
+                        if (lane == 0) litn[vb >> 5] = lmk;
                     }
                 }
                 // ---------------- cell phase of shell k: lit cells are compacted into a
@@ -473,10 +583,16 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                 for (int base = warp * 32; base < nround; base += NT) {
                     int c = base + lane;
                     bool lit = false;
+                    int vi[3];
+                    bool any = false;
                     if (c < ncell) {
-                        // a cell contributes iff one of its furthest vertices has radiance
-                        int vi[3];
                         cell_verts(c, vi);
+                        const unsigned* lmk = litm + (k & 1) * LW;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) any |= ((lmk[vi[q] >> 5] >> (vi[q] & 31)) & 1u) != 0u;
+                    }
+                    if (any) {
+                        // a cell contributes iff one of its furthest vertices has radiance
                         float tq[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
@@ -612,6 +728,10 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
                 double hn = sqrt(h[0] * h[0] + h[3] * h[3] + h[5] * h[5] + 2.0 * (h[1] * h[1] + h[2] * h[2] + h[4] * h[4]));
                 o.kappa[rec] = (float)((double)tot[30] / hn);
             }
+            if (o.radii || o.axes)
+                write_ellipsoid(h, lam, LY, !finite || !isfinite(LY) || !isfinite(lmax), (double)a.eps, (double)a.r_min,
+                                (double)a.r_max, o.radii ? o.radii + 3 * rec : nullptr,
+                                o.axes ? o.axes + 9 * rec : nullptr);
         }
         __syncthreads();
     }
@@ -620,7 +740,7 @@ __global__ void __launch_bounds__(NT) k_records(DevScene sc, RecArgs a) {
 size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
     return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
-           (size_t)nw * 64 * 4;
+           (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32) * 4;
 }
 
 template <int NT>

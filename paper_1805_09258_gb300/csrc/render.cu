@@ -111,6 +111,7 @@ struct GridView {
     const int* start;
     const int* list;
     int G;
+    const float4* ell;   // ellipsoidal records' region matrices, NULL for spheres
 };
 
 __device__ __forceinline__ float3 cache_lookup(const GridView& g, float3 x, int& cnt) {
@@ -127,8 +128,17 @@ __device__ __forceinline__ float3 cache_lookup(const GridView& g, float3 x, int&
         float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
         float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (!(d2 < a.w * a.w)) continue;
+        float dd;
+        if (g.ell) {   // ellipsoidal distance ratio sqrt(D^T M D)
+            float4 m0 = __ldg(&g.ell[2 * k]), m1 = __ldg(&g.ell[2 * k + 1]);
+            float r2e = fmaf(m0.x * dx, dx, fmaf(m0.w * dy, dy, m1.y * dz * dz)) +
+                        2.0f * fmaf(m0.y * dx, dy, fmaf(m0.z * dx, dz, m1.x * dy * dz));
+            if (!(r2e < 1.0f)) continue;
+            dd = 1.0f - sqrtf(fmaxf(r2e, 0.f));
+        } else {
+            dd = 1.0f - sqrtf(d2) / a.w;
+        }
         float4 r1 = __ldg(&g.rec[4 * k + 1]), r2 = __ldg(&g.rec[4 * k + 2]), r3 = __ldg(&g.rec[4 * k + 3]);
-        float dd = 1.0f - sqrtf(d2) / a.w;
         float w = dd * dd * fmaf(-2.0f, dd, 3.0f);
         ar = fmaf(w, r1.x + fmaf(r1.w, dx, fmaf(r2.x, dy, r2.y * dz)), ar);
         ag = fmaf(w, r1.y + fmaf(r2.z, dx, fmaf(r2.w, dy, r3.x * dz)), ag);
@@ -346,7 +356,7 @@ extern "C" int vrc_render(vrc_scene* s, const vrc_grid* grid, const vrc_camera* 
     if ((long long)w * h == 0) return VRC_OK;
     Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
     if (grid->order != 1) return VRC_ERR_INVALID;
-    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G};
+    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G, grid->aniso ? grid->ell : nullptr};
     int n = w * h;
     k_render<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, x0, y0, w, h, steps, d_img, d_miss,
                                                                   nullptr, 0);
@@ -449,7 +459,7 @@ extern "C" int vrc_render_pixels(vrc_scene* s, const vrc_grid* grid, const vrc_c
     if (n_pix == 0) return VRC_OK;
     if (!d_pix || !d_img) return VRC_ERR_INVALID;
     Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
-    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G};
+    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G, grid->aniso ? grid->ell : nullptr};
     k_render<<<(n_pix + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, 0, 0, 0, 0, steps, d_img, d_miss,
                                                                       d_pix, n_pix);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;

@@ -69,6 +69,9 @@ struct vrc_grid {
     int order;             // 1 or 2
     float4* rec;           // [n][4]: (pos, R), (L, g_r.x), (g_r.y, g_r.z, g_g.x, g_g.y), (g_g.z, g_b)
     float4* hess;          // [n][5]: 18 Hessian entries (order 2), padded
+    int aniso;             // 1: ellipsoidal records (rec .w = largest principal radius)
+    float4* ell;           // [n][2]: region matrix M (xx, xy, xz, yy), (yz, zz, -, -) when aniso
+    float4* ext;           // [n]: bounding-box half extents and largest radius when aniso
     int* cell_start;       // [G^3 + 1]
     int* cell_list;        // [entries]
     long long entries;

@@ -38,18 +38,19 @@ class PlacementResult:
 
 def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, mlp: MLP = None,
           coarse_params=None, cell_over_radius: float = 1.0, capacity: int = None, valid=None,
-          base: PlacementResult = None, predict_level: int = 5) -> PlacementResult:
+          base: PlacementResult = None, predict_level: int = 5, aniso: bool = False) -> PlacementResult:
     """Place records until every candidate point `cand` [n,3] (CUDA float32) is covered.
 
     valid [n] (int32, nullable): only nonzero entries are candidates.  base: an earlier
     placement whose records are kept (the new records are appended after them).
+    aniso: records cover their ellipsoids (anisotropic cache points) instead of spheres.
     """
     torch = _torch()
     n = cand.shape[0]
     t0 = time.perf_counter()
     prev = 0 if base is None else base.n_records
     cap = capacity or (prev + n)
-    recs = alloc_records(cap, full=False)
+    recs = alloc_records(cap, full=False, aniso=aniso)
     if prev:
         for k, v in base.records.items():
             recs[k][:prev].copy_(v)
@@ -89,7 +90,7 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         compute_records(scene, pts[:m].contiguous(), params, out=out)
         total += m
         view = {k: v[:total] for k, v in recs.items()}
-        grid = Grid(view, n=total)
+        grid = Grid(view, n=total, aniso=aniso)
         query_inscatter(grid, cand, rgb, count)
         update_coverage(count, level)
 

@@ -26,13 +26,15 @@ class FrameResult:
 
 
 def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int = 4, mlp=None, coarse_params=None,
-                 cell_over_radius: float = 1.5, start_level: int = 2, max_level: int = 7, max_repairs: int = 8):
+                 cell_over_radius: float = 1.5, start_level: int = 2, max_level: int = 7, max_repairs: int = 8,
+                 aniso: bool = False):
     torch = _torch()
     W, H = cam.width, cam.height
     t0 = time.perf_counter()
     w, h = (W + stride - 1) // stride, (H + stride - 1) // stride
     pts, valid = march_points(scene, cam, 0, 0, w, h, stride, steps)
-    pl = place(scene, params, pts, start_level, max_level, mlp, coarse_params, cell_over_radius, valid=valid)
+    pl = place(scene, params, pts, start_level, max_level, mlp, coarse_params, cell_over_radius, valid=valid,
+               aniso=aniso)
     passes = [("prepass", int(pts.shape[0]), pl.n_records)]
     img = torch.empty((W * H, 3), dtype=torch.float32, device="cuda")
     miss = torch.empty((W * H,), dtype=torch.int32, device="cuda")
@@ -49,7 +51,7 @@ def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int
         mpts, mvalid = march_pixels(scene, cam, plist, steps)
         before = pl.n_records
         pl = place(scene, params, mpts, max_level, max_level, None, None, cell_over_radius, valid=mvalid, base=pl,
-                   capacity=pl.n_records + int(mpts.shape[0]))
+                   capacity=pl.n_records + int(mpts.shape[0]), aniso=aniso)
         passes.append(("repair", m, pl.n_records - before))
         render_pixels(scene, pl.grid, cam, plist, steps, img, miss)
     torch.cuda.synchronize()
