@@ -335,10 +335,10 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                 "record_status": {"ok": int((st == 0).sum()), "clamped": int(((st & 6) != 0).sum()),
                                   "nonfinite": int(((st & 1) != 0).sum())},
                 "peaks_file": bool(peaks)}
-        # kernels launched per step: 1 memset-free counter reset is a cudaMemset (not ours);
-        # records 1, grid: pack + count + 3 scan + fill + sort = 7, queries: 3 scan + bin +
-        # scatter + query = 6
-        line["gpu_launches"] = args.steps * (1 + 7 + 6)
+        # kernels launched per step (the work-counter reset is a cudaMemset, not ours):
+        # records + radius = 2, grid: pack + count + 3 scan + fill + sort = 7, queries:
+        # 3 scan + bin + scatter + query = 6
+        line["gpu_launches"] = args.steps * (2 + 7 + 6)
         if not args.no_cpu_baseline:
             n_rec, n_q = w.n_records, min(w.n_queries, 131072)
             rr, qr, spent = oracle_rates(w, n_rec, n_q, os.cpu_count() or 1)
@@ -424,12 +424,13 @@ def run_render(args, w):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     out = {}
-    runs = [("learned", mlp, rp.eps, False), ("learned_aniso", mlp, rp.eps, True)]
-    runs += [(f"plain_eps{e:g}", None, e, False) for e in (rp.eps, rp.eps / 2, rp.eps / 4)]
-    runs += [(f"plain_aniso_eps{e:g}", None, e, True) for e in (rp.eps, rp.eps / 2)]
-    for name, net, eps, aniso in runs:
+    runs = [("learned", mlp, rp.eps, False, False), ("learned_aniso", mlp, rp.eps, True, False)]
+    runs += [(f"plain_eps{e:g}", None, e, False, False) for e in (rp.eps, rp.eps / 2, rp.eps / 4)]
+    runs += [(f"plain_aniso_eps{e:g}", None, e, True, False) for e in (rp.eps, rp.eps / 2)]
+    runs += [(f"plain_split_eps{e:g}", None, e, False, True) for e in (rp.eps, rp.eps / 2)]
+    for name, net, eps, aniso, split in runs:
         rpe = W.configs.replace(rp, eps=eps)
-        kw = dict(steps=steps, stride=8, mlp=net, coarse_params=coarse, aniso=aniso)
+        kw = dict(steps=steps, stride=8, mlp=net, coarse_params=coarse, aniso=aniso, split=split)
         render_frame(scene, cam, rpe, **kw)     # warm-up
         out[name] = render_frame(scene, cam, rpe, **kw)
     # reference crop: a full record at every march point of the central 64 x 64 pixels
@@ -445,11 +446,41 @@ def run_render(args, w):
     orc = oracle.records(oracle.OracleScene(w.scene), rp_ref, pn, rec_ids=idx, track_margins=1)
     Lg = full["L"].cpu().numpy()[idx].astype(np.float64)
     spot = float(np.max(np.abs(Lg - orc["L"]) / (1e-4 * np.abs(orc["L"]) + orc["bud_L"] + 1e-12)))
+    # frame-wide error: 8 march points of each of 2,048 seeded pixels, a full record at
+    # each (the same 32x64 reference records), against each frame's cache look-up there
+    rng = np.random.default_rng(77)
+    n_pix = ex["width"] * ex["height"]
+    spix = torch.from_numpy(np.sort(rng.choice(n_pix, 2048, replace=False)).astype(np.int32)).cuda()
+    mp, mv = vrc.march_pixels(scene, cam, spix, steps)
+    sel = torch.arange(0, mp.shape[0], steps // 8, device=mp.device)
+    sel = sel[mv[sel] != 0]
+    spts = mp[sel].contiguous()
+    sref = vrc.compute_records(scene, spts, rp_ref, full=False)["L"].cpu().numpy().astype(np.float64)
+    # noise floor: the same reference with another jitter seed
+    rp_ref2 = W.configs.replace(rp_ref, seed=W.configs.SEED_JITTER + 8)
+    sref2 = vrc.compute_records(scene, spts, rp_ref2, full=False)["L"].cpu().numpy().astype(np.float64)
+
+    def point_errors(L):
+        # L1-relative error over all points (robust to the few points next to the light,
+        # whose 1/d^2 single scattering dominates any RMS) and the median per-point error
+        d = np.abs(L - sref).sum(axis=1)
+        m = np.abs(sref).sum(axis=1)
+        return float(d.sum() / m.sum()), float(np.median(d / np.maximum(m, 1e-12)))
+
+    floor_l1, floor_med = point_errors(sref2)
     res = {}
     for name, fr in out.items():
+        rgb, cnt = vrc.query_inscatter(fr.placement.grid, spts)
+        if fr.placement2 is not None:
+            rgb2, cnt2 = vrc.query_inscatter(fr.placement2.grid, spts)
+            rgb = rgb + rgb2
+        point_l1, point_med = point_errors(rgb.cpu().numpy().astype(np.float64))
         img = fr.image.cpu().numpy().reshape(ex["height"], ex["width"], 3)[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3)
         st = fr.placement.records["status"].cpu().numpy()
         res[name] = {"frame_ms": fr.seconds * 1e3, "records": fr.n_records, "passes": len(fr.passes),
+                     "point_rel_l1_vs_full_records": point_l1, "point_median_rel_err": point_med,
+                     "records_ss_ms": None if fr.placement2 is None else [fr.placement.n_records,
+                                                                          fr.placement2.n_records],
                      "rel_rmse_vs_full_records": float(np.sqrt(np.mean((img - ref) ** 2)) / np.mean(np.abs(ref))),
                      "crop_mean": float(np.mean(img)), "crop_max": float(np.max(img)),
                      "records_clamped_lo": float(np.mean((st & 2) != 0)), "misses_repaired": fr.misses}
@@ -461,8 +492,11 @@ def run_render(args, w):
                                             "pixels": ex["width"] * ex["height"], "march_steps": steps,
                                             "record_rays": rp.n_rays, "prepass_stride": 8},
             "mlp_training_s": train_s,
-            "reference": "full record (32x64 rays) at every march point of the central 64x64 crop",
+            "reference": "full record (32x64 rays) at every march point of the central 64x64 crop; and at "
+                         f"{int(spts.shape[0])} march points of 2,048 seeded pixels (point errors)",
             "oracle_spot_check_max_err_over_tol": spot,
+            "point_noise_floor": {"rel_l1": floor_l1, "median_rel_err": floor_med,
+                                  "what": "two 32x64 references with different jitter at the same points"},
             "reference_crop_mean": float(np.mean(ref)), "reference_crop_max": float(np.max(ref)),
             "reference_zero_L_fraction": float(np.mean(np.all(full["L"].cpu().numpy() == 0, axis=1))),
             "spot_L": orc["L"][:, 1].tolist()}

@@ -80,7 +80,11 @@ void vrc_destroy_scene(vrc_scene* scene);
  *   ff_signed         1: signed solid angle (closes every shell); 0: |A| as printed in App. C
  *   extrap_order      1 (Eq. radianceTaylor) or 2 (adds the Hessian term); used by the grid
  *   r_min, r_max      radius clamps
- *   rec_base          jitter index of record 0 (record i uses rec_base + i) */
+ *   rec_base          jitter index of record 0 (record i uses rec_base + i)
+ *   parts             0: the whole in-scattered radiance (surface and medium shells);
+ *                     1: surface shell only (the single-scattering cache of Sec. 6);
+ *                     2: medium shells only (the multiple-scattering cache of Sec. 6).
+ *                     With 1 or 2 every output (L, grad, hess, radius, ...) is that part. */
 typedef struct {
     int32_t n_bands, n_bins;
     float dt, eps;
@@ -90,6 +94,7 @@ typedef struct {
     int32_t extrap_order;
     float r_min, r_max;
     int64_t rec_base;
+    int32_t parts;
 } vrc_record_params;
 
 /* Caller-allocated device outputs of vrc_compute_records, one row per record.
@@ -158,8 +163,10 @@ typedef struct {
  * their derivatives, reduce them into L, grad L and H L, and set each radius from the
  * Hessian's eigenvalues.  d_n_bands [n] (nullable) gives per-record band counts with
  * bins = 2 * bands (mixed ray counts in one persistent launch).  Asynchronous on
- * `stream`.  VRC_ERR_INVALID for null required outputs, n < 0, bands < 1, bins < 3;
- * VRC_ERR_UNSUPPORTED for more than 256 bands or 512 bins. */
+ * `stream`.  The radius stage (luminance eigen-solve, Eq. radiusAniso3D) runs as a
+ * second kernel on the same stream.  VRC_ERR_INVALID for null required outputs, n < 0,
+ * bands < 1, bins < 3, parts outside 0..2; VRC_ERR_UNSUPPORTED for more than 256 bands
+ * or 512 bins. */
 int vrc_compute_records(vrc_scene* scene, const float* d_pos, int32_t n, const int32_t* d_n_bands,
                         const vrc_record_params* params, const vrc_records_view* d_out, void* stream);
 
@@ -175,7 +182,8 @@ int vrc_get_record_tuning(const vrc_scene* scene, vrc_record_tuning* tuning);
 /* Autotuner for the record kernel's launch shape (threads per block, bands per chunk).
  * Times each candidate on up to 16,384 of the given records (one warm-up launch and two
  * timed launches each, CUDA events on `stream`), keeps the fastest in the scene, writes
- * it to *best and caches it per (bands, bins, mixed-count flag, log2 of n).  A cached
+ * it to *best and caches it per (bands, bins, mixed-count flag, parts, log2 of n, log2
+ * of the scene's triangle count).  A cached
  * entry is reused without timing.  d_out is overwritten by the trial launches (its final
  * contents are a correct evaluation of the first records).  Synchronous. */
 int vrc_autotune_records(vrc_scene* scene, const float* d_pos, int32_t n, const int32_t* d_n_bands,
@@ -223,6 +231,37 @@ int vrc_build_record_grid_aniso(const vrc_records_view* recs, int32_t n, int32_t
 int vrc_query_inscatter(const vrc_grid* grid, const float* d_q, int32_t nq, float* d_rgb, int32_t* d_status,
                         void* stream);
 
+/* --------------------------------------------------------------- 2D world
+ * The paper's two-dimensional world (Sec. 3; Sec. 4 in 2D; App. A; App. B; Eq.
+ * radiusAniso2D): light travels, scatters and is absorbed in the plane, radiance from a
+ * point source falls off as 1/r, the isotropic phase function is 1/(2 pi).  Geometry is
+ * a set of line segments (two-sided Lambertian curves, BRDF albedo / 2) in the unit
+ * square, which the homogeneous medium fills. */
+typedef struct { float pos[2]; float intensity[3]; } vrc2d_point_light;
+typedef struct vrc2d_scene vrc2d_scene;
+
+/* Upload a 2D scene: segs [n][4] (x0, y0, x1, y1), albedo [n][3] (host arrays, copied);
+ * sigma_s, sigma_a of the medium; up to VRC_MAX_LIGHTS point lights.  VRC_ERR_INVALID for
+ * a zero-length segment or bad sizes.  Synchronous. */
+int vrc2d_build_scene(const float* segs, int32_t n_segs, const float* albedo, float sigma_s, float sigma_a,
+                      const vrc2d_point_light* lights, int32_t n_lights, vrc2d_scene** out);
+void vrc2d_destroy_scene(vrc2d_scene* scene);
+
+/* n 2D records at d_pos [n][2] (device): N = params->n_bins equal-angle strata with one
+ * jittered ray each (params->n_bands must be 1), distance shells every params->dt, every
+ * shell's cells (segments between angularly adjacent vertices) with App. B's angle
+ * derivatives and App. A's transmittance derivatives, the radius of Eq. radiusAniso2D.
+ * Results go to `out` in the 3D layout of vrc_records_view, in the plane z = 0.5: pos
+ * (x, y, 0.5), grad [c] = (d/dx, d/dy, 0), hess [c] = (xx, xy, 0, yy, 0, 0), eig = the
+ * 2D eigenvalues and 0 in ascending order, radii / axes = the ellipse's principal radii
+ * (Eq. radiusAniso2D per eigenvalue) with the plane's normal as third axis (radius
+ * r_max), so vrc_build_record_grid(_aniso) and vrc_query_inscatter answer 2D queries at
+ * z = 0.5.  params->parts selects surface shell / medium shells as for 3D records.
+ * Asynchronous on `stream`.  VRC_ERR_INVALID for bad parameters; VRC_ERR_UNSUPPORTED for
+ * more than 4096 directions. */
+int vrc2d_compute_records(vrc2d_scene* scene, const float* d_pos, int32_t n, const vrc_record_params* params,
+                          const vrc_records_view* out, void* stream);
+
 /* --------------------------------------------------------------- renderer
  * The renderer around the cache (Sec. 6): camera rays marched through the medium with the
  * paper's uniform ray marching, cache look-ups at the march points, adaptive placement.
@@ -240,17 +279,20 @@ int vrc_march_points(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_
 
 /* Render the w x h pixel rectangle at (x0, y0) from an order-1 grid: d_img [w*h][3]; d_miss
  * [w*h] (nullable) = march points of the pixel that no record covers (they contribute 0).
+ * grid2 (nullable): a second order-1 grid whose look-up is added to the first -- the
+ * separate single- and multiple-scattering caches of Sec. 6 (records computed with
+ * parts 1 and 2); a march point then counts once in d_miss per cache that misses it.
  * Asynchronous. */
-int vrc_render(vrc_scene* scene, const vrc_grid* grid, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w,
-               int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
+int vrc_render(vrc_scene* scene, const vrc_grid* grid, const vrc_grid* grid2, const vrc_camera* cam, int32_t x0,
+               int32_t y0, int32_t w, int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
 
 /* The same for a list of pixels (linear index y * width + x): march points [n_pix*steps][3]
  * in list order; render writes each listed pixel at its own index of the full-frame
  * d_img [width*height][3] / d_miss.  Asynchronous. */
 int vrc_march_pixels(vrc_scene* scene, const vrc_camera* cam, const int32_t* d_pix, int32_t n_pix, int32_t steps,
                      float* d_pts, int32_t* d_valid, void* stream);
-int vrc_render_pixels(vrc_scene* scene, const vrc_grid* grid, const vrc_camera* cam, const int32_t* d_pix,
-                      int32_t n_pix, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
+int vrc_render_pixels(vrc_scene* scene, const vrc_grid* grid, const vrc_grid* grid2, const vrc_camera* cam,
+                      const int32_t* d_pix, int32_t n_pix, int32_t steps, float* d_img, int32_t* d_miss, void* stream);
 
 /* Indices i (ascending) with d_flags[i] != 0 into d_idx; their number to *h_count
  * (synchronous).  d_scratch holds 2 n + n/1024 + 2 ints. */

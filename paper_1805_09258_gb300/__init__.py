@@ -39,7 +39,8 @@ class _Light(C.Structure):
 class RecordParamsC(C.Structure):
     _fields_ = [("n_bands", C.c_int32), ("n_bins", C.c_int32), ("dt", C.c_float), ("eps", C.c_float),
                 ("omega_o", C.c_float * 3), ("seed", C.c_uint64), ("ff_signed", C.c_int32),
-                ("extrap_order", C.c_int32), ("r_min", C.c_float), ("r_max", C.c_float), ("rec_base", C.c_int64)]
+                ("extrap_order", C.c_int32), ("r_min", C.c_float), ("r_max", C.c_float), ("rec_base", C.c_int64),
+                ("parts", C.c_int32)]
 
 
 class RecordsView(C.Structure):
@@ -80,6 +81,10 @@ def load_library(path: Optional[str] = None):
     L.vrc_graph_destroy.restype = None
     L.vrc_get_record_tuning.argtypes = [P, P]
     L.vrc_build_record_grid.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
+    L.vrc2d_build_scene.argtypes = [P, I32, P, C.c_float, C.c_float, P, I32, C.POINTER(C.c_void_p)]
+    L.vrc2d_destroy_scene.argtypes = [P]
+    L.vrc2d_destroy_scene.restype = None
+    L.vrc2d_compute_records.argtypes = [P, P, I32, P, P, P]
     L.vrc_build_record_grid_aniso.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
     L.vrc_destroy_grid.argtypes = [P]
     L.vrc_destroy_grid.restype = None
@@ -87,13 +92,13 @@ def load_library(path: Optional[str] = None):
     L.vrc_query_inscatter_noalloc.argtypes = [P, I32, I32, P, I32, P, P, P]
     L.vrc_coarse_features.argtypes = [P, P, I32, P, P, P]
     L.vrc_march_points.argtypes = [P, P, I32, I32, I32, I32, I32, I32, P, P, P]
-    L.vrc_render.argtypes = [P, P, P, I32, I32, I32, I32, I32, P, P, P]
+    L.vrc_render.argtypes = [P, P, P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_composite.argtypes = [P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_select_sites.argtypes = [P, P, I32, I32, P, C.c_int64, P, P, P, P]
     L.vrc_update_coverage.argtypes = [P, I32, P, P]
     L.vrc_init_levels.argtypes = [P, I32, I32, P, P]
     L.vrc_march_pixels.argtypes = [P, P, P, I32, I32, P, P, P]
-    L.vrc_render_pixels.argtypes = [P, P, P, P, I32, I32, P, P, P]
+    L.vrc_render_pixels.argtypes = [P, P, P, P, P, I32, I32, P, P, P]
     L.vrc_compact_indices.argtypes = [P, I32, P, C.c_int64, P, P, P]
     L.vrc_levels_by_cell.argtypes = [P, I32, I32, P, P, P, I32, C.c_float, I32, I32, P, P, P]
     L.vrc_levels_from_radius.argtypes = [P, I32, C.c_float, I32, I32, P, P]
@@ -146,6 +151,7 @@ def record_params(rp) -> RecordParamsC:
     p.ff_signed, p.extrap_order = int(rp.ff_signed), int(rp.extrap_order)
     p.r_min, p.r_max = float(rp.r_min), float(rp.r_max)
     p.rec_base = int(getattr(rp, "rec_base", 0))
+    p.parts = int(getattr(rp, "parts", 0))
     return p
 
 
@@ -256,6 +262,62 @@ def compute_records(scene: Scene, pos, params, n_bands=None, out: Optional[dict]
     rc = load_library().vrc_compute_records(scene.handle, _ptr(pos), n, nbp, C.byref(p), C.byref(v),
                                             _stream_ptr(stream))
     _check(rc, "vrc_compute_records")
+    return out
+
+
+class _Light2(C.Structure):
+    _fields_ = [("pos", C.c_float * 2), ("intensity", C.c_float * 3)]
+
+
+class Scene2D:
+    """A scene of the 2D world on the device (vrc2d_build_scene / vrc2d_destroy_scene):
+    segments [n, 4] (x0, y0, x1, y1), albedo [n, 3], medium sigma_s / sigma_a, point lights
+    with .pos (2) and .intensity (3)."""
+
+    def __init__(self, segs, albedo, sigma_s, sigma_a, lights):
+        L = load_library()
+        segs = np.ascontiguousarray(segs, dtype=np.float32).reshape(-1, 4)
+        n = segs.shape[0]
+        albedo = np.ascontiguousarray(albedo, dtype=np.float32).reshape(n, 3)
+        nl = len(lights)
+        larr = (_Light2 * max(nl, 1))()
+        for i, l in enumerate(lights):
+            larr[i].pos[:] = [float(v) for v in l.pos]
+            larr[i].intensity[:] = [float(v) for v in l.intensity]
+        h = C.c_void_p()
+        rc = L.vrc2d_build_scene(segs.ctypes.data if n else None, n, albedo.ctypes.data if n else None,
+                                 float(sigma_s), float(sigma_a), C.byref(larr), nl, C.byref(h))
+        _check(rc, "vrc2d_build_scene")
+        self.handle = h
+        self.n_segs = n
+
+    @classmethod
+    def from_workload(cls, scene):
+        return cls(scene.segs, scene.albedo, scene.sigma_s, scene.sigma_a, scene.lights)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) and _lib is not None:
+                _lib.vrc2d_destroy_scene(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def compute_records_2d(scene: Scene2D, pos, params, out: Optional[dict] = None, full: bool = True,
+                       stream=None) -> dict:
+    """vrc2d_compute_records on device positions pos [n, 2]: records in the 3D layout in
+    the plane z = 0.5 (see vrc.h)."""
+    torch = _torch()
+    assert pos.is_cuda and pos.dtype == torch.float32 and pos.is_contiguous() and pos.shape[1] == 2
+    n = pos.shape[0]
+    if out is None:
+        out = alloc_records(n, full=full, device=pos.device)
+    v = records_view(out)
+    p = record_params(params)
+    rc = load_library().vrc2d_compute_records(scene.handle, _ptr(pos), n, C.byref(p), C.byref(v),
+                                              _stream_ptr(stream))
+    _check(rc, "vrc2d_compute_records")
     return out
 
 
@@ -483,13 +545,17 @@ def march_points(scene: Scene, cam: Camera, x0, y0, w, h, stride, steps, stream=
     return pts, valid
 
 
-def render(scene: Scene, grid: "Grid", cam: Camera, x0, y0, w, h, steps, img=None, miss=None, stream=None):
+def render(scene: Scene, grid: "Grid", cam: Camera, x0, y0, w, h, steps, img=None, miss=None, stream=None,
+           grid2: "Grid" = None):
+    """vrc_render; grid2 (optional) is a second cache whose look-up is added (separate
+    single- and multiple-scattering caches)."""
     torch = _torch()
     if img is None:
         img = torch.empty((w * h, 3), dtype=torch.float32, device="cuda")
     if miss is None:
         miss = torch.empty((w * h,), dtype=torch.int32, device="cuda")
-    _check(load_library().vrc_render(scene.handle, grid.handle, C.byref(cam), x0, y0, w, h, steps, _ptr(img),
+    g2 = grid2.handle if grid2 is not None else None
+    _check(load_library().vrc_render(scene.handle, grid.handle, g2, C.byref(cam), x0, y0, w, h, steps, _ptr(img),
                                      _ptr(miss), _stream_ptr(stream)), "vrc_render")
     return img, miss
 
@@ -504,9 +570,10 @@ def march_pixels(scene: Scene, cam: Camera, pix, steps, stream=None):
     return pts, valid
 
 
-def render_pixels(scene: Scene, grid: "Grid", cam: Camera, pix, steps, img, miss, stream=None):
-    _check(load_library().vrc_render_pixels(scene.handle, grid.handle, C.byref(cam), _ptr(pix), pix.shape[0], steps,
-                                            _ptr(img), _ptr(miss), _stream_ptr(stream)), "vrc_render_pixels")
+def render_pixels(scene: Scene, grid: "Grid", cam: Camera, pix, steps, img, miss, stream=None, grid2: "Grid" = None):
+    g2 = grid2.handle if grid2 is not None else None
+    _check(load_library().vrc_render_pixels(scene.handle, grid.handle, g2, C.byref(cam), _ptr(pix), pix.shape[0],
+                                            steps, _ptr(img), _ptr(miss), _stream_ptr(stream)), "vrc_render_pixels")
 
 
 def compact_indices(flags, scratch, out, stream=None) -> int:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvrc.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["scene.cu", "records.cu", "query.cu", "noalloc.cu", "mlp.cu", "render.cu"]
+SOURCES = ["scene.cu", "records.cu", "query.cu", "noalloc.cu", "mlp.cu", "render.cu", "flat.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

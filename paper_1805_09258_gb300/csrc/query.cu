@@ -77,11 +77,14 @@ __device__ __forceinline__ bool sphere_meets_cell(float3 c, float R, int ix, int
 }
 
 // count (fill = false) or fill (fill = true) the cells each record's sphere overlaps;
-// with `ext` (ellipsoidal records) only the cells within its bounding box
+// with `ext` (ellipsoidal records) only the cells within its bounding box.  One warp per
+// record, its lanes over the cells of the record's box: a record meets hundreds of cells,
+// and the lanes' atomics are then in flight together.
 template <bool FILL>
 __global__ void k_insert(const float4* rec, const float4* ext, int n, int G, int* counts, const int* start,
                          int* list) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
     if (k >= n) return;
     float4 a = rec[4 * k];
     float3 c = make_float3(a.x, a.y, a.z);
@@ -95,14 +98,16 @@ __global__ void k_insert(const float4* rec, const float4* ext, int n, int G, int
     int x0 = max(0, (int)floorf((c.x - ex) * G)), x1 = min(G - 1, (int)floorf((c.x + ex) * G));
     int y0 = max(0, (int)floorf((c.y - ey) * G)), y1 = min(G - 1, (int)floorf((c.y + ey) * G));
     int z0 = max(0, (int)floorf((c.z - ez) * G)), z1 = min(G - 1, (int)floorf((c.z + ez) * G));
-    for (int ix = x0; ix <= x1; ++ix)
-        for (int iy = y0; iy <= y1; ++iy)
-            for (int iz = z0; iz <= z1; ++iz) {
-                if (!sphere_meets_cell(c, R, ix, iy, iz, h)) continue;
-                int cell = (ix * G + iy) * G + iz;
-                int slot = atomicAdd(&counts[cell], 1);
-                if (FILL) list[start[cell] + slot] = k;
-            }
+    int ny = y1 - y0 + 1, nz = z1 - z0 + 1;
+    int total = (x1 - x0 + 1) * ny * nz;
+    for (int t = lane; t < total; t += 32) {
+        int ix = x0 + t / (ny * nz), r = t % (ny * nz);
+        int iy = y0 + r / nz, iz = z0 + r % nz;
+        if (!sphere_meets_cell(c, R, ix, iy, iz, h)) continue;
+        int cell = (ix * G + iy) * G + iz;
+        int slot = atomicAdd(&counts[cell], 1);
+        if (FILL) list[start[cell] + slot] = k;
+    }
 }
 
 // Sort each cell's list ascending (a deterministic summation order for the queries).
@@ -340,7 +345,8 @@ int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, 
         k_pack<<<nbk, tb, 0, st>>>(*v, n, order, g->rec, g->hess);
         if (aniso) k_pack_ellipsoid<<<nbk, tb, 0, st>>>(*v, n, g->rec, g->ell, g->ext);
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
-        k_insert<false><<<nbk, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, nullptr, nullptr);
+        int nwb = (int)(((long long)n * 32 + tb - 1) / tb);   // one warp per record
+        k_insert<false><<<nwb, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, nullptr, nullptr);
         exclusive_scan(g->q_count, ncell, g->cell_start, g->scan_tmp, st);
         int total = 0;
         if (cudaMemcpyAsync(&total, g->cell_start + ncell, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -354,7 +360,7 @@ int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, 
             return rc;
         }
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
-        k_insert<true><<<nbk, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, g->cell_start, g->cell_list);
+        k_insert<true><<<nwb, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, g->cell_start, g->cell_list);
         k_sort_lists<<<ncell, 256, 0, st>>>(g->cell_start, ncell, g->cell_list);
     } else {
         cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);

@@ -41,6 +41,7 @@ struct RecArgs {
     int cap;                     // shared-memory vertex capacity per chunk
     int* counter;                // work counter (reset before the launch)
     const int* order;            // nullable: work item -> record (largest ray sets first)
+    int parts;                   // 0 all shells, 1 surface shell only, 2 medium shells only
 };
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 float te;
                 if (prim >= 0) {
                     te = th;
-                    Lo = surface_radiance(sc, prim, x + d * te, d);
+                    if (a.parts != 2) Lo = surface_radiance(sc, prim, x + d * te, d);
                 } else {
                     te = cube_exit_dev(x, d);
                 }
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
             }
             atomicMax(&misc[0], __float_as_int(tmax_loc));   // non-negative floats order as ints
             __syncthreads();
-            const int K = (int)ceilf(__int_as_float(misc[0]) / a.dt);
+            const int K = a.parts == 1 ? 0 : (int)ceilf(__int_as_float(misc[0]) / a.dt);
             kmax_rec = max(kmax_rec, K);
             // cells of this chunk
             const int nq = r1e - r0;                         // quad bands with upper row in [r0, r1e)
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 };
                 int* wqw = wq + warp * 64;
                 int qn = 0;
-                const int nround = (ncell + 31) & ~31;
+                const int nround = (a.parts == 2 && k == 0) ? 0 : (ncell + 31) & ~31;   // MS cache: no surface shell
                 for (int base = warp * 32; base < nround; base += NT) {
                     int c = base + lane;
                     bool lit = false;
@@ -685,53 +686,26 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
             if (o.L_ms) o.L_ms[3 * rec + ch] = lm;
             o.pos[3 * rec + ch] = ch == 0 ? x.x : (ch == 1 ? x.y : x.z);
         } else if (tid == 64) {
-            // luminance Hessian, FP64 eigenvalues and radius (Eq. radiusAniso3D)
-            const double Y[3] = {0.2126, 0.7152, 0.0722};
-            double h[6];
+            // finiteness, degeneracy and conditioning; the radius comes from k_radius
             bool finite = true;
-            for (int e = 0; e < 6; ++e) {
-                h[e] = Y[0] * (double)tot[12 + e] + Y[1] * (double)tot[18 + e] + Y[2] * (double)tot[24 + e];
-            }
-            double LY = 0.0;
-            for (int ch = 0; ch < 3; ++ch)
-                LY += Y[ch] * ((double)tot[96 + ch] + (double)tot[99 + ch] * (double)wms);
             for (int e = 0; e < 32; ++e)
                 if (e != 30 && e != 31 && !isfinite(tot[e])) finite = false;
             for (int e = 0; e < 6; ++e)
                 if (!isfinite(tot[96 + e])) finite = false;
-            double lam[3];
-            eig3_sym(h, lam);
-            double lmax = fmax(fabs(lam[0]), fmax(fabs(lam[1]), fabs(lam[2])));
-            int status = 0;
-            double R;
-            if (!finite || !isfinite(LY) || !isfinite(lmax)) { status |= VRC_REC_NONFINITE | VRC_REC_CLAMP_LO; R = a.r_min; }
-            else if (!(LY > 0.0)) { status |= VRC_REC_CLAMP_LO; R = a.r_min; }
-            else if (lmax == 0.0) { status |= VRC_REC_CLAMP_HI; R = a.r_max; }
-            else {
-                R = pow(15.0 * LY * (double)a.eps / (4.0 * 3.14159265358979323846 * lmax), 0.2);
-                if (R < a.r_min) { status |= VRC_REC_CLAMP_LO; R = a.r_min; }
-                if (R > a.r_max) { status |= VRC_REC_CLAMP_HI; R = a.r_max; }
-            }
+            int status = finite ? 0 : VRC_REC_NONFINITE;
             if (tot[31] + tot[63] > 0.f) status |= VRC_REC_DEGENERATE;
-            o.radius[rec] = (float)R;
-            if (o.log_radius) o.log_radius[rec] = (float)log(R);
             o.status[rec] = status;
             if (o.n_cells) o.n_cells[rec] = misc[1];
             if (o.n_far) o.n_far[rec] = misc[3];
             if (o.n_shells) o.n_shells[rec] = kmax_rec;
-            if (o.eig) {
-                o.eig[3 * rec] = (float)lam[0];
-                o.eig[3 * rec + 1] = (float)lam[1];
-                o.eig[3 * rec + 2] = (float)lam[2];
-            }
             if (o.kappa) {
+                const double Y[3] = {0.2126, 0.7152, 0.0722};
+                double h[6];
+                for (int e = 0; e < 6; ++e)
+                    h[e] = Y[0] * (double)tot[12 + e] + Y[1] * (double)tot[18 + e] + Y[2] * (double)tot[24 + e];
                 double hn = sqrt(h[0] * h[0] + h[3] * h[3] + h[5] * h[5] + 2.0 * (h[1] * h[1] + h[2] * h[2] + h[4] * h[4]));
                 o.kappa[rec] = (float)((double)tot[30] / hn);
             }
-            if (o.radii || o.axes)
-                write_ellipsoid(h, lam, LY, !finite || !isfinite(LY) || !isfinite(lmax), (double)a.eps, (double)a.r_min,
-                                (double)a.r_max, o.radii ? o.radii + 3 * rec : nullptr,
-                                o.axes ? o.axes + 9 * rec : nullptr);
         }
         __syncthreads();
     }
@@ -741,6 +715,46 @@ size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
     return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
            (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32) * 4;
+}
+
+// Radius stage, one thread per record after the record kernel (its FP64 work would
+// otherwise run on one thread of each block while the others wait): the Rec.709
+// luminance of the stored L and Hessian, FP64 eigenvalues, the isotropic radius from
+// the largest |eigenvalue| and, when asked for, the ellipsoid (Eq. radiusAniso3D).
+__global__ void k_radius(RecArgs a) {
+    int rec = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rec >= a.n) return;
+    const vrc_records_view& o = a.out;
+    const double Y[3] = {0.2126, 0.7152, 0.0722};
+    const float* H = o.hess + 18 * (size_t)rec;
+    double h[6];
+    for (int e = 0; e < 6; ++e) h[e] = Y[0] * (double)H[e] + Y[1] * (double)H[6 + e] + Y[2] * (double)H[12 + e];
+    double LY = Y[0] * (double)o.L[3 * rec] + Y[1] * (double)o.L[3 * rec + 1] + Y[2] * (double)o.L[3 * rec + 2];
+    int status = o.status[rec];
+    double lam[3];
+    eig3_sym(h, lam);
+    double lmax = fmax(fabs(lam[0]), fmax(fabs(lam[1]), fabs(lam[2])));
+    bool bad = (status & VRC_REC_NONFINITE) || !isfinite(LY) || !isfinite(lmax);
+    double R;
+    if (bad) { status |= VRC_REC_NONFINITE | VRC_REC_CLAMP_LO; R = a.r_min; }
+    else if (!(LY > 0.0)) { status |= VRC_REC_CLAMP_LO; R = a.r_min; }
+    else if (lmax == 0.0) { status |= VRC_REC_CLAMP_HI; R = a.r_max; }
+    else {
+        R = pow(15.0 * LY * (double)a.eps / (4.0 * 3.14159265358979323846 * lmax), 0.2);
+        if (R < a.r_min) { status |= VRC_REC_CLAMP_LO; R = a.r_min; }
+        if (R > a.r_max) { status |= VRC_REC_CLAMP_HI; R = a.r_max; }
+    }
+    o.radius[rec] = (float)R;
+    if (o.log_radius) o.log_radius[rec] = (float)log(R);
+    o.status[rec] = status;
+    if (o.eig) {
+        o.eig[3 * rec] = (float)lam[0];
+        o.eig[3 * rec + 1] = (float)lam[1];
+        o.eig[3 * rec + 2] = (float)lam[2];
+    }
+    if (o.radii || o.axes)
+        write_ellipsoid(h, lam, LY, bad, (double)a.eps, (double)a.r_min, (double)a.r_max,
+                        o.radii ? o.radii + 3 * rec : nullptr, o.axes ? o.axes + 9 * rec : nullptr);
 }
 
 template <int NT>
@@ -758,6 +772,7 @@ int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st)
     DevScene dv = s->dev;
     dv.use_lb = s->tuning.shadow_bvh ? 0 : 1;
     kfn<<<grid, NT, smem, st>>>(dv, a);
+    k_radius<<<(a.n + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
@@ -818,6 +833,7 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     int nb = p->n_bands, ns = d_n_bands ? 2 * p->n_bands : p->n_bins;
     if (nb < 1 || ns < 3 || !(p->dt > 0.f) || !(p->eps > 0.f) || !(p->r_min > 0.f) || !(p->r_max >= p->r_min))
         return VRC_ERR_INVALID;
+    if (p->parts < 0 || p->parts > 2) return VRC_ERR_INVALID;
     if (nb > 256 || ns > 512) return VRC_ERR_UNSUPPORTED;
     if ((out->hit_prim != nullptr) != (out->hit_t != nullptr)) return VRC_ERR_INVALID;
     if (out->hit_prim && out->dbg_stride < nb * ns + 2) return VRC_ERR_INVALID;
@@ -852,6 +868,7 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.cap = cap;
     a.counter = s->d_counter;
     a.order = nullptr;
+    a.parts = p->parts;
     VRC_CUDA_CHECK(cudaMemsetAsync(s->d_counter, 0, sizeof(int), st));
     if (d_n_bands && n > 1) {
         // largest ray sets first; the order and histogram live in scene-owned scratch
@@ -959,8 +976,10 @@ extern "C" void vrc_graph_destroy(vrc_graph* g) {
 
 // ----------------------------------------------------------------- autotuner
 namespace {
+// cached winners, keyed by ray set, mixed counts, record parts, log2 of the record count
+// and log2 of the scene's triangle count
 struct TuneEntry {
-    int nb, ns, mixed, logn;
+    int nb, ns, mixed, parts, logn, logt;
     vrc_record_tuning t;
 };
 std::mutex g_tune_mutex;
@@ -974,10 +993,13 @@ extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n,
     int logn = 0;
     while ((1 << (logn + 1)) <= n) ++logn;
     const int mixed = d_n_bands ? 1 : 0;
+    int logt = 0;
+    while ((1 << (logt + 1)) <= s->n_prims) ++logt;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (const TuneEntry& e : g_tune_cache)
-            if (e.nb == p->n_bands && e.ns == p->n_bins && e.mixed == mixed && e.logn == logn) {
+            if (e.nb == p->n_bands && e.ns == p->n_bins && e.mixed == mixed && e.parts == p->parts && e.logn == logn &&
+                e.logt == logt) {
                 s->tuning = e.t;
                 if (best) *best = e.t;
                 return VRC_OK;
@@ -1015,6 +1037,6 @@ extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n,
     s->tuning = top;
     if (best) *best = top;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache.push_back({p->n_bands, p->n_bins, mixed, logn, top});
+    g_tune_cache.push_back({p->n_bands, p->n_bins, mixed, p->parts, logn, logt, top});
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }

@@ -151,9 +151,11 @@ __device__ __forceinline__ float3 cache_lookup(const GridView& g, float3 x, int&
 }
 
 // one thread per pixel: march, look up, accumulate; misses counted per pixel.  With a
-// pixel list, thread i renders pixel pix[i] and writes at that pixel's index.
-__global__ void k_render(DevScene sc, Cam c, GridView g, int x0, int y0, int w, int h, int steps, float* img,
-                         int* miss, const int* pix, int n_pix) {
+// pixel list, thread i renders pixel pix[i] and writes at that pixel's index.  With a
+// second grid (g2.rec != NULL) the radiance is the sum of both caches' look-ups and a
+// march point counts as a miss once per cache that has no record for it.
+__global__ void k_render(DevScene sc, Cam c, GridView g, GridView g2, int x0, int y0, int w, int h, int steps,
+                         float* img, int* miss, const int* pix, int n_pix) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (pix ? n_pix : w * h)) return;
     int px, py;
@@ -175,6 +177,10 @@ __global__ void k_render(DevScene sc, Cam c, GridView g, int x0, int y0, int w, 
             int cnt;
             float3 L = cache_lookup(g, x, cnt);
             if (cnt == 0) ++nmiss;
+            if (g2.rec) {
+                L = L + cache_lookup(g2, x, cnt);
+                if (cnt == 0) ++nmiss;
+            }
             acc = acc + L * (ds * sc.sigma_s * __expf(-sc.sigma_t * s));
         }
     }
@@ -350,16 +356,20 @@ extern "C" int vrc_march_points(vrc_scene* s, const vrc_camera* cam, int32_t x0,
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
-extern "C" int vrc_render(vrc_scene* s, const vrc_grid* grid, const vrc_camera* cam, int32_t x0, int32_t y0, int32_t w,
-                          int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream) {
+static GridView grid_view(const vrc_grid* g) {
+    if (!g) return GridView{nullptr, nullptr, nullptr, 1, nullptr};
+    return GridView{g->rec, g->cell_start, g->cell_list, g->G, g->aniso ? g->ell : nullptr};
+}
+
+extern "C" int vrc_render(vrc_scene* s, const vrc_grid* grid, const vrc_grid* grid2, const vrc_camera* cam, int32_t x0,
+                          int32_t y0, int32_t w, int32_t h, int32_t steps, float* d_img, int32_t* d_miss, void* stream) {
     if (!s || !grid || !cam || w < 0 || h < 0 || steps < 1 || !d_img) return VRC_ERR_INVALID;
     if ((long long)w * h == 0) return VRC_OK;
     Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
-    if (grid->order != 1) return VRC_ERR_INVALID;
-    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G, grid->aniso ? grid->ell : nullptr};
+    if (grid->order != 1 || (grid2 && grid2->order != 1)) return VRC_ERR_INVALID;
     int n = w * h;
-    k_render<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, x0, y0, w, h, steps, d_img, d_miss,
-                                                                  nullptr, 0);
+    k_render<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, grid_view(grid), grid_view(grid2), x0, y0,
+                                                                  w, h, steps, d_img, d_miss, nullptr, 0);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
@@ -453,15 +463,16 @@ extern "C" int vrc_march_pixels(vrc_scene* s, const vrc_camera* cam, const int32
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
-extern "C" int vrc_render_pixels(vrc_scene* s, const vrc_grid* grid, const vrc_camera* cam, const int32_t* d_pix,
-                                 int32_t n_pix, int32_t steps, float* d_img, int32_t* d_miss, void* stream) {
+extern "C" int vrc_render_pixels(vrc_scene* s, const vrc_grid* grid, const vrc_grid* grid2, const vrc_camera* cam,
+                                 const int32_t* d_pix, int32_t n_pix, int32_t steps, float* d_img, int32_t* d_miss,
+                                 void* stream) {
     if (!s || !grid || !cam || n_pix < 0 || steps < 1 || grid->order != 1) return VRC_ERR_INVALID;
+    if (grid2 && grid2->order != 1) return VRC_ERR_INVALID;
     if (n_pix == 0) return VRC_OK;
     if (!d_pix || !d_img) return VRC_ERR_INVALID;
     Cam c = make_cam(cam->pos, cam->forward, cam->vfov_deg, cam->width, cam->height);
-    GridView gv{grid->rec, grid->cell_start, grid->cell_list, grid->G, grid->aniso ? grid->ell : nullptr};
-    k_render<<<(n_pix + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, gv, 0, 0, 0, 0, steps, d_img, d_miss,
-                                                                      d_pix, n_pix);
+    k_render<<<(n_pix + 127) / 128, 128, 0, (cudaStream_t)stream>>>(s->dev, c, grid_view(grid), grid_view(grid2), 0, 0,
+                                                                      0, 0, steps, d_img, d_miss, d_pix, n_pix);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 

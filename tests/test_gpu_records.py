@@ -167,3 +167,44 @@ def test_light_buffer_shadow_rays_match_bvh_shadow_rays(vrc):
             diff = np.abs(a[k] - b[k]).max(axis=1)
             scale = np.abs(b[k]).max(axis=1) + 1e-12
             assert np.mean(diff <= 1e-5 * scale) > 0.95, k
+
+
+def test_single_and_multiple_scattering_parts(vrc):
+    """parts = 1 (surface shell) and parts = 2 (medium shells) give the single- and
+    multiple-scattering records of Sec. 6's two caches: bit for bit the parts of the whole
+    record, and their radii follow their own luminance and Hessian (oracle, Eq.
+    radiusAniso3D)."""
+    w = W.config1()
+    pos = w.positions()
+    whole = run_gpu(vrc, w.scene, w.params, pos)
+    ref = O.records(O.OracleScene(w.scene), w.params, pos, track_margins=1)
+    Y = np.array([0.2126, 0.7152, 0.0722])
+    for parts, sfx in ((1, "_ss"), (2, "_ms")):
+        p = W.configs.replace(w.params, parts=parts)
+        g = run_gpu(vrc, w.scene, p, pos)
+        for k in ("L", "grad", "hess"):
+            assert np.array_equal(g[k], whole[k + sfx]), (parts, k)
+            assert np.array_equal(g[k + sfx], whole[k + sfx]), (parts, k)
+        other = "_ms" if parts == 1 else "_ss"
+        assert np.all(g["L" + other] == 0) and np.all(g["hess" + other] == 0)
+        if parts == 1:
+            assert np.all(g["n_shells"] == 0)
+        # radius of the part from the oracle's part (tolerances as for the whole record)
+        part_ref = dict(ref)
+        part_ref["L"], part_ref["hess"] = ref["L" + sfx], ref["hess" + sfx]
+        for r in range(pos.shape[0]):
+            LY = float(Y @ ref["L" + sfx][r])
+            hy = (Y[:, None] * ref["hess" + sfx][r].reshape(3, 6)).sum(0)
+            R, st, lam = O.radius(LY, hy, p.eps, p.r_min, p.r_max)
+            part_ref.setdefault("_R", []).append(R)
+            part_ref.setdefault("_lam", []).append(np.abs(lam).max())
+            part_ref.setdefault("_LY", []).append(LY)
+            part_ref.setdefault("_st", []).append(st)
+        part_ref["radius"] = np.array(part_ref["_R"])
+        part_ref["lam_max"] = np.array(part_ref["_lam"])
+        part_ref["L_Y"] = np.array(part_ref["_LY"])
+        part_ref["status"] = np.array(part_ref["_st"])
+        compare_radius(g, part_ref)
+    invalid = W.configs.replace(w.params, parts=3)
+    with pytest.raises(vrc.VrcError):
+        run_gpu(vrc, w.scene, invalid, pos[:2])

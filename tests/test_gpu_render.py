@@ -97,3 +97,50 @@ def test_frame_has_no_uncovered_points_and_tracks_the_full_record_image(vrc):
     # the reference composites one noisy 512-ray record per march point; the cached image
     # interpolates between records, so part of this gap is the reference's own noise
     assert rel < 0.35
+
+
+def test_split_caches_frame(vrc):
+    """Separate single- and multiple-scattering caches (Sec. 6): both caches hold records,
+    no march point is left uncovered by either, and the frame tracks the full records."""
+    from paper_1805_09258_gb300.renderer import render_frame
+    w = W.config2()
+    s = vrc.Scene.from_workload(w.scene)
+    rp = RecordParams(n_bands=16, n_bins=32, omega_o=(0.0, -1.0, 0.0))
+    Wd, Hd, steps = 192, 108, 32
+    c = vrc.Camera.make((0.5, -0.8, 0.5), (0.0, 1.0, 0.0), 45.0, Wd, Hd)
+    fr = render_frame(s, c, rp, steps=steps, stride=4, split=True)
+    assert fr.placement.n_records > 0 and fr.placement2.n_records > 0
+    _, miss = vrc.render(s, fr.placement.grid, c, 0, 0, Wd, Hd, steps, grid2=fr.placement2.grid)
+    assert int(miss.sum()) == 0
+    x0, y0, cw = Wd // 2 - 16, Hd // 2 - 16, 32
+    pts, _ = vrc.march_points(s, c, x0, y0, cw, cw, 1, steps)
+    full = vrc.compute_records(s, pts, rp, full=False)
+    ref = vrc.composite(s, c, x0, y0, cw, cw, steps, full["L"]).cpu().numpy()
+    img = fr.image.cpu().numpy().reshape(Hd, Wd, 3)[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3)
+    rel = np.sqrt(np.mean((img - ref) ** 2)) / np.mean(np.abs(ref))
+    print("records", fr.placement.n_records, fr.placement2.n_records, "relative RMSE vs full records", rel)
+    assert rel < 0.35
+
+
+def test_second_grid_adds_its_lookup(vrc):
+    """Two constant caches: the image is the sum of the two one-cache images, and a point
+    that only one cache covers counts as one miss."""
+    sc = Scene(tris=np.zeros((0, 3, 3), np.float32), albedo=np.zeros((0, 3), np.float32),
+               medium=Medium(0.4, 0.1, 0.0), lights=[PointLight((0.5, 0.5, 0.9), (1, 1, 1))])
+    s = vrc.Scene.from_workload(sc)
+    c = vrc.Camera.make((0.5, -0.8, 0.5), (0.0, 1.0, 0.0), 45.0, 48, 27)
+
+    def const_grid(L, R):
+        rec = {k: torch.zeros(shape, device="cuda") for k, shape in
+               (("pos", (1, 3)), ("L", (1, 3)), ("grad", (1, 9)), ("radius", (1,)))}
+        rec["pos"][0] = torch.tensor([0.5, 0.5, 0.5])
+        rec["L"][0] = torch.tensor(L)
+        rec["radius"][0] = R
+        return vrc.Grid(rec)
+
+    ga, gb = const_grid([1.0, 0.5, 0.25], 10.0), const_grid([0.1, 0.2, 0.3], 0.3)
+    ia, ma = vrc.render(s, ga, c, 0, 0, 48, 27, 16)
+    ib, mb = vrc.render(s, gb, c, 0, 0, 48, 27, 16)
+    iab, mab = vrc.render(s, ga, c, 0, 0, 48, 27, 16, grid2=gb)
+    assert torch.allclose(iab, ia + ib, rtol=1e-6, atol=1e-7)
+    assert torch.equal(mab, ma + mb) and int(mb.sum()) > 0

@@ -44,6 +44,7 @@ class RecordParams:
     r_min: float = 1e-3
     r_max: float = 0.5
     rec_base: int = 0
+    parts: int = 0          # 0 whole radiance, 1 surface shell (SS cache), 2 medium shells (MS cache)
 
     @property
     def n_rays(self) -> int:
