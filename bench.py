@@ -396,9 +396,12 @@ def run_batching(args, w):
 
 def run_render(args, w):
     """Extra measurement (not the default line): one 1920x1080 frame of the render-shaped
-    workload, plain vs learned placement with spherical or ellipsoidal records, RMSE against
-    a crop composited from a full record at every march point (those records spot-checked
-    against the FP64 oracle)."""
+    workload, plain vs learned placement (and ellipsoidal / split-cache variants), each at
+    several error tolerances, with the frame's error measured on 16 crops of 16x16 pixels
+    spread over the frame against a reference composited from a 64x128-ray record at every
+    march point of those pixels (records spot-checked against the FP64 oracle).  The
+    equal-error comparison interpolates the plain path's frame time at each learned run's
+    error (log-log between the two nearest plain tolerances)."""
     import torch
     import oracle
     import oracle.mlp as M
@@ -410,8 +413,8 @@ def run_render(args, w):
     rp = w.params
     coarse = W.RecordParams(n_bands=8, n_bins=16, seed=W.configs.SEED_JITTER + 1000, omega_o=rp.omega_o)
     scene = vrc.Scene.from_workload(w.scene)
-    cam = vrc.Camera.make(ex["camera"], ex["forward"], ex["vfov_deg"], ex["width"], ex["height"])
-    steps = ex["steps"]
+    Wd, Hd, steps = ex["width"], ex["height"], ex["steps"]
+    cam = vrc.Camera.make(ex["camera"], ex["forward"], ex["vfov_deg"], Wd, Hd)
     # train the predictor on records of 4 render-style scenes (other seeds)
     t0 = time.perf_counter()
     exs = learned.ExampleSet(4 * 16384)
@@ -423,83 +426,85 @@ def run_render(args, w):
     learned.train(mlp, F, T, steps=1500, batch=4096, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    out = {}
-    runs = [("learned", mlp, rp.eps, False, False), ("learned_aniso", mlp, rp.eps, True, False)]
-    runs += [(f"plain_eps{e:g}", None, e, False, False) for e in (rp.eps, rp.eps / 2, rp.eps / 4)]
-    runs += [(f"plain_aniso_eps{e:g}", None, e, True, False) for e in (rp.eps, rp.eps / 2)]
-    runs += [(f"plain_split_eps{e:g}", None, e, False, True) for e in (rp.eps, rp.eps / 2)]
+    # reference: 16 crops of 16 x 16 pixels on a 4 x 4 lattice over the frame
+    cw = 16
+    crops = [(int((i + 0.5) * Wd / 4) - cw // 2, int((j + 0.5) * Hd / 4) - cw // 2) for j in range(4) for i in range(4)]
+    rp_ref = W.configs.replace(rp, n_bands=64, n_bins=128, seed=W.configs.SEED_JITTER + 7)
+    rp_ref2 = W.configs.replace(rp_ref, seed=W.configs.SEED_JITTER + 8)
+    refs, refs2, pts_all = [], [], []
+    for (x0, y0) in crops:
+        pts, valid = vrc.march_points(scene, cam, x0, y0, cw, cw, 1, steps)
+        pts_all.append(pts)
+        for rr, dst in ((rp_ref, refs), (rp_ref2, refs2)):
+            full = vrc.compute_records(scene, pts, rr, full=False)
+            dst.append(vrc.composite(scene, cam, x0, y0, cw, cw, steps, full["L"]).cpu().numpy())
+    ref = np.concatenate(refs)
+    ref2 = np.concatenate(refs2)
+
+    def rel_rmse(img):
+        return float(np.sqrt(np.mean((img - ref) ** 2)) / np.mean(np.abs(ref)))
+
+    floor = rel_rmse(ref2)
+    # FP64 oracle spot check of reference records
+    pn = pts_all[5].cpu().numpy()
+    idx = np.arange(0, pn.shape[0], pn.shape[0] // 8)[:8]
+    orc = oracle.records(oracle.OracleScene(w.scene), rp_ref, pn[idx], rec_ids=idx, track_margins=1)
+    full = vrc.compute_records(scene, pts_all[5], rp_ref, full=False)
+    Lg = full["L"].cpu().numpy()[idx].astype(np.float64)
+    spot = float(np.max(np.abs(Lg - orc["L"]) / (1e-4 * np.abs(orc["L"]) + orc["bud_L"] + 1e-12)))
+    # the runs
+    tols = (rp.eps * 2, rp.eps, rp.eps / 2)
+    runs = [(f"plain_eps{e:g}", None, e, False, False) for e in tols]
+    runs += [(f"learned_eps{e:g}", mlp, e, False, False) for e in tols]
+    runs += [(f"plain_aniso_eps{e:g}", None, e, True, False) for e in tols[:2]]
+    runs += [(f"learned_aniso_eps{e:g}", mlp, e, True, False) for e in tols[:2]]
+    runs += [(f"plain_split_eps{rp.eps:g}", None, rp.eps, False, True)]
+    res = {}
     for name, net, eps, aniso, split in runs:
         rpe = W.configs.replace(rp, eps=eps)
         kw = dict(steps=steps, stride=8, mlp=net, coarse_params=coarse, aniso=aniso, split=split)
         render_frame(scene, cam, rpe, **kw)     # warm-up
-        out[name] = render_frame(scene, cam, rpe, **kw)
-    # reference crop: a full record at every march point of the central 64 x 64 pixels
-    cw = 64
-    x0, y0 = ex["width"] // 2 - cw // 2, ex["height"] // 2 - cw // 2
-    pts, valid = vrc.march_points(scene, cam, x0, y0, cw, cw, 1, steps)
-    rp_ref = W.configs.replace(rp, n_bands=32, n_bins=64, seed=W.configs.SEED_JITTER + 7)   # 4x the rays, own jitter
-    full = vrc.compute_records(scene, pts, rp_ref, full=False)
-    ref = vrc.composite(scene, cam, x0, y0, cw, cw, steps, full["L"]).cpu().numpy()
-    # FP64 oracle spot check of reference records
-    idx = np.arange(0, pts.shape[0], pts.shape[0] // 8)[:8]
-    pn = pts.cpu().numpy()[idx]
-    orc = oracle.records(oracle.OracleScene(w.scene), rp_ref, pn, rec_ids=idx, track_margins=1)
-    Lg = full["L"].cpu().numpy()[idx].astype(np.float64)
-    spot = float(np.max(np.abs(Lg - orc["L"]) / (1e-4 * np.abs(orc["L"]) + orc["bud_L"] + 1e-12)))
-    # frame-wide error: 8 march points of each of 2,048 seeded pixels, a full record at
-    # each (the same 32x64 reference records), against each frame's cache look-up there
-    rng = np.random.default_rng(77)
-    n_pix = ex["width"] * ex["height"]
-    spix = torch.from_numpy(np.sort(rng.choice(n_pix, 2048, replace=False)).astype(np.int32)).cuda()
-    mp, mv = vrc.march_pixels(scene, cam, spix, steps)
-    sel = torch.arange(0, mp.shape[0], steps // 8, device=mp.device)
-    sel = sel[mv[sel] != 0]
-    spts = mp[sel].contiguous()
-    sref = vrc.compute_records(scene, spts, rp_ref, full=False)["L"].cpu().numpy().astype(np.float64)
-    # noise floor: the same reference with another jitter seed
-    rp_ref2 = W.configs.replace(rp_ref, seed=W.configs.SEED_JITTER + 8)
-    sref2 = vrc.compute_records(scene, spts, rp_ref2, full=False)["L"].cpu().numpy().astype(np.float64)
-
-    def point_errors(L):
-        # L1-relative error over all points (robust to the few points next to the light,
-        # whose 1/d^2 single scattering dominates any RMS) and the median per-point error
-        d = np.abs(L - sref).sum(axis=1)
-        m = np.abs(sref).sum(axis=1)
-        return float(d.sum() / m.sum()), float(np.median(d / np.maximum(m, 1e-12)))
-
-    floor_l1, floor_med = point_errors(sref2)
-    res = {}
-    for name, fr in out.items():
-        rgb, cnt = vrc.query_inscatter(fr.placement.grid, spts)
-        if fr.placement2 is not None:
-            rgb2, cnt2 = vrc.query_inscatter(fr.placement2.grid, spts)
-            rgb = rgb + rgb2
-        point_l1, point_med = point_errors(rgb.cpu().numpy().astype(np.float64))
-        img = fr.image.cpu().numpy().reshape(ex["height"], ex["width"], 3)[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3)
-        st = fr.placement.records["status"].cpu().numpy()
-        res[name] = {"frame_ms": fr.seconds * 1e3, "records": fr.n_records, "passes": len(fr.passes),
-                     "point_rel_l1_vs_full_records": point_l1, "point_median_rel_err": point_med,
+        fr = render_frame(scene, cam, rpe, **kw)
+        im = fr.image.cpu().numpy().reshape(Hd, Wd, 3)
+        img = np.concatenate([im[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3) for (x0, y0) in crops])
+        res[name] = {"frame_ms": fr.seconds * 1e3, "records": fr.n_records, "rel_rmse": rel_rmse(img),
+                     "eps": eps, "passes": len(fr.passes), "misses_repaired": fr.misses,
                      "records_ss_ms": None if fr.placement2 is None else [fr.placement.n_records,
-                                                                          fr.placement2.n_records],
-                     "rel_rmse_vs_full_records": float(np.sqrt(np.mean((img - ref) ** 2)) / np.mean(np.abs(ref))),
-                     "crop_mean": float(np.mean(img)), "crop_max": float(np.max(img)),
-                     "records_clamped_lo": float(np.mean((st & 2) != 0)), "misses_repaired": fr.misses}
-    n_q = ex["width"] * ex["height"] * steps
-    line = {"metric": METRIC, "value": n_q / (out["learned"].seconds), "unit": "march points/s (whole frame)",
-            "runs": res,
+                                                                          fr.placement2.n_records]}
+    # equal-error comparison: plain frame time interpolated at each learned run's error
+    plain = sorted((v["rel_rmse"], v["frame_ms"], v["records"]) for k, v in res.items() if k.startswith("plain_eps"))
+    equal = {}
+    for k, v in res.items():
+        if not k.startswith("learned_eps"):
+            continue
+        e = v["rel_rmse"]
+        lo = [p for p in plain if p[0] <= e]
+        hi = [p for p in plain if p[0] >= e]
+        if lo and hi:
+            a, b = lo[-1], hi[0]
+            if a[0] == b[0]:
+                t, n = a[1], a[2]
+            else:
+                f_ = (math.log(e) - math.log(a[0])) / (math.log(b[0]) - math.log(a[0]))
+                t = math.exp(math.log(a[1]) + f_ * (math.log(b[1]) - math.log(a[1])))
+                n = math.exp(math.log(a[2]) + f_ * (math.log(b[2]) - math.log(a[2])))
+            equal[k] = {"rel_rmse": e, "plain_frame_ms_at_equal_error": t, "learned_frame_ms": v["frame_ms"],
+                        "speedup": t / v["frame_ms"], "plain_records_at_equal_error": n,
+                        "learned_records": v["records"]}
+        else:
+            equal[k] = {"rel_rmse": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
+    n_q = Wd * Hd * steps
+    base = res[f"learned_eps{rp.eps:g}"]
+    line = {"metric": METRIC, "value": n_q / (base["frame_ms"] * 1e-3), "unit": "march points/s (whole frame)",
+            "runs": res, "equal_error": equal,
             "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": "f32 (f64 eigen-solve)",
             "data": "synthetic", "config": {"workload": w.name, "scene_tris": w.scene.n_tris,
-                                            "pixels": ex["width"] * ex["height"], "march_steps": steps,
+                                            "pixels": Wd * Hd, "march_steps": steps,
                                             "record_rays": rp.n_rays, "prepass_stride": 8},
             "mlp_training_s": train_s,
-            "reference": "full record (32x64 rays) at every march point of the central 64x64 crop; and at "
-                         f"{int(spts.shape[0])} march points of 2,048 seeded pixels (point errors)",
-            "oracle_spot_check_max_err_over_tol": spot,
-            "point_noise_floor": {"rel_l1": floor_l1, "median_rel_err": floor_med,
-                                  "what": "two 32x64 references with different jitter at the same points"},
-            "reference_crop_mean": float(np.mean(ref)), "reference_crop_max": float(np.max(ref)),
-            "reference_zero_L_fraction": float(np.mean(np.all(full["L"].cpu().numpy() == 0, axis=1))),
-            "spot_L": orc["L"][:, 1].tolist()}
+            "reference": "64x128-ray record at every march point of 16 crops of 16x16 pixels (4x4 lattice)",
+            "reference_noise_floor_rel_rmse": floor,
+            "oracle_spot_check_max_err_over_tol": spot}
     print(json.dumps(line), flush=True)
 
 

@@ -82,7 +82,8 @@ def check_radius(g, ref, idx, p):
         assert abs(rr[0] - Rg) <= 1e-6 * Rg
         ax = g["axes"][i].reshape(3, 3)
         zrow = int(np.argmax(np.abs(ax[:, 2])))
-        assert abs(g["radii"][i, zrow] - p.r_max) <= 1e-7 and abs(ax[zrow, 2]) == 1.0
+        rz = p.r_max if LY > 0 else p.r_min          # a black record is r_min on every axis
+        assert abs(g["radii"][i, zrow] - rz) <= 1e-7 and abs(ax[zrow, 2]) == 1.0
 
 
 def test_small_scene_all_records(vrc):

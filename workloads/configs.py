@@ -6,7 +6,7 @@
 | mid (config2) | 170 random boxes + ground, 2,048 tris | 4,096 | 32 x 64 | 1M |
 | batching (config3) | 8,333 boxes + ground, 100,000 tris | 100,000 | 8x16 .. 64x128 log-uniform | - |
 | learned (config4) | 16 mid-style scenes | training set | 32 x 64 (+ coarse 8 x 16) | - |
-| render (config5) | 20,833 boxes + ground, 250,000 tris | adaptive | 16 x 32 | 1920x1080x64 |
+| render (config5) | 20,833 boxes + ground, 250,000 tris | adaptive | 32 x 64 | 1920x1080x64 |
 
 Common settings: medium fills the unit cube, one point light at (0.5, 0.5, 0.92)
 with RGB intensity (1.0, 0.9, 0.8), Lambertian surfaces of albedo 0.7, march
@@ -164,7 +164,7 @@ def config5() -> Workload:
     """Render-shaped workload: 250,000 triangles, 1920x1080 camera, 64 march steps."""
     scene = render_scene()
     return Workload("render: 250k tris, 1920x1080x64 march points", scene,
-                    RecordParams(n_bands=16, n_bins=32, omega_o=(0.0, -1.0, 0.0)),
+                    RecordParams(n_bands=32, n_bins=64, omega_o=(0.0, -1.0, 0.0)),
                     n_records=0, n_queries=1920 * 1080 * 64,
                     extra={"camera": (0.5, -0.8, 0.5), "forward": (0.0, 1.0, 0.0), "vfov_deg": 45.0,
                            "width": 1920, "height": 1080, "steps": 64})
