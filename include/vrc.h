@@ -45,6 +45,7 @@ extern "C" {
 #define VRC_REC_CLAMP_LO 2      /* radius clamped to r_min (or L <= 0) */
 #define VRC_REC_CLAMP_HI 4      /* radius clamped to r_max (or a zero Hessian) */
 #define VRC_REC_DEGENERATE 8    /* at least one cell had A = B = 0 and was skipped */
+#define VRC_REC_BAD_COUNT 16    /* per-record band count outside [2, params n_bands]: not computed */
 
 /* --------------------------------------------------------------- scene */
 /* Homogeneous medium (Sec. 3, Table 1): scattering and absorption coefficients and
@@ -155,6 +156,9 @@ typedef struct {
     int32_t chunk_bands;    /* bands of the ray set kept in shared memory at once */
     int32_t blocks_per_sm;  /* persistent blocks per SM */
     int32_t shadow_bvh;     /* 1: shadow rays traverse the BVH; 0: light buffer (default) */
+    int32_t no_prepass;     /* 1: the record kernel traces its primary rays itself; 0 (default):
+                               uniform ray sets of up to 64 Mi rays per call are traced first by
+                               a flat pre-pass kernel into scene-owned buffers (28 B per ray) */
 } vrc_record_tuning;
 
 /* Compute n records at d_pos [n][3] (Secs. 4-5 and App. A, C): trace the stratified
@@ -162,7 +166,9 @@ typedef struct {
  * occluders), evaluate every cell's form factor, transmittance and phase terms with
  * their derivatives, reduce them into L, grad L and H L, and set each radius from the
  * Hessian's eigenvalues.  d_n_bands [n] (nullable) gives per-record band counts with
- * bins = 2 * bands (mixed ray counts in one persistent launch).  Asynchronous on
+ * bins = 2 * bands (mixed ray counts in one persistent launch); each must lie in
+ * [2, params->n_bands] (shared memory is sized for params->n_bands), a record outside
+ * that range gets zero outputs and status VRC_REC_BAD_COUNT.  Asynchronous on
  * `stream`.  The radius stage (luminance eigen-solve, Eq. radiusAniso3D) runs as a
  * second kernel on the same stream.  VRC_ERR_INVALID for null required outputs, n < 0,
  * bands < 1, bins < 3, parts outside 0..2; VRC_ERR_UNSUPPORTED for more than 256 bands
@@ -179,7 +185,17 @@ int vrc_compute_records_host(vrc_scene* scene, const float* h_pos, int32_t n, co
 int vrc_set_record_tuning(vrc_scene* scene, const vrc_record_tuning* tuning);
 int vrc_get_record_tuning(const vrc_scene* scene, vrc_record_tuning* tuning);
 
-/* Autotuner for the record kernel's launch shape (threads per block, bands per chunk).
+/* Per-kernel timing of vrc_compute_records (no counterpart in the paper; measurement).
+ * vrc_record_timing(scene, 1) starts recording CUDA events on the launching stream around
+ * the three kernels of each call (primary pre-pass, record kernel, radius stage) -- at most
+ * 64 calls, none while the stream is captured into a graph; 0 stops.  vrc_record_kernel_times
+ * waits for the recorded events, writes the summed milliseconds of the three kernels to
+ * ms3[3] and the number of timed calls to *launches, and clears the record. */
+int vrc_record_timing(vrc_scene* scene, int32_t enable);
+int vrc_record_kernel_times(vrc_scene* scene, float* ms3, int32_t* launches);
+
+/* Autotuner for the record kernel's launch shape (threads per block, bands per chunk and,
+ * for uniform ray sets, the primary pre-pass on or off).
  * Times each candidate on up to 16,384 of the given records (one warm-up launch and two
  * timed launches each, CUDA events on `stream`), keeps the fastest in the scene, writes
  * it to *best and caches it per (bands, bins, mixed-count flag, parts, log2 of n, log2

@@ -52,7 +52,7 @@ class RecordsView(C.Structure):
 
 class RecordTuning(C.Structure):
     _fields_ = [("threads", C.c_int32), ("chunk_bands", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("shadow_bvh", C.c_int32)]
+                ("shadow_bvh", C.c_int32), ("no_prepass", C.c_int32)]
 
 
 _lib = None
@@ -74,6 +74,8 @@ def load_library(path: Optional[str] = None):
     L.vrc_compute_records.argtypes = [P, P, I32, P, P, P, P]
     L.vrc_compute_records_host.argtypes = [P, P, I32, P, P, P, P, P, P]
     L.vrc_set_record_tuning.argtypes = [P, P]
+    L.vrc_record_timing.argtypes = [P, I32]
+    L.vrc_record_kernel_times.argtypes = [P, P, P]
     L.vrc_autotune_records.argtypes = [P, P, I32, P, P, P, P, P]
     L.vrc_records_graph_create.argtypes = [P, P, I32, P, P, P, C.POINTER(C.c_void_p)]
     L.vrc_graph_launch.argtypes = [P, P]
@@ -183,8 +185,19 @@ class Scene:
     def from_workload(cls, scene):
         return cls(scene.tris, scene.albedo, scene.medium, scene.lights, scene.emission)
 
-    def set_tuning(self, threads=0, chunk_bands=0, blocks_per_sm=0, shadow_bvh=0):
-        t = RecordTuning(threads, chunk_bands, blocks_per_sm, shadow_bvh)
+    def record_timing(self, enable: bool = True):
+        """vrc_record_timing: CUDA events around the kernels of each compute_records call."""
+        _check(load_library().vrc_record_timing(self.handle, int(enable)), "vrc_record_timing")
+
+    def kernel_times(self):
+        """vrc_record_kernel_times: (summed ms of pre-pass, record kernel, radius stage; calls)."""
+        ms = (C.c_float * 3)()
+        n = C.c_int32(0)
+        _check(load_library().vrc_record_kernel_times(self.handle, ms, C.byref(n)), "vrc_record_kernel_times")
+        return [float(v) for v in ms], int(n.value)
+
+    def set_tuning(self, threads=0, chunk_bands=0, blocks_per_sm=0, shadow_bvh=0, no_prepass=0):
+        t = RecordTuning(threads, chunk_bands, blocks_per_sm, shadow_bvh, no_prepass)
         _check(load_library().vrc_set_record_tuning(self.handle, C.byref(t)), "vrc_set_record_tuning")
 
     def get_tuning(self):
@@ -329,7 +342,8 @@ def autotune_records(scene: Scene, pos, params, out: dict, n_bands=None, stream=
     rc = load_library().vrc_autotune_records(scene.handle, _ptr(pos), pos.shape[0], _ptr(n_bands), C.byref(p),
                                              C.byref(v), _stream_ptr(stream), C.byref(t))
     _check(rc, "vrc_autotune_records")
-    return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm, shadow_bvh=t.shadow_bvh)
+    return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm, shadow_bvh=t.shadow_bvh,
+                no_prepass=t.no_prepass)
 
 
 class RecordsGraph:

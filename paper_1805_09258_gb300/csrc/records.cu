@@ -42,6 +42,8 @@ struct RecArgs {
     int* counter;                // work counter (reset before the launch)
     const int* order;            // nullable: work item -> record (largest ray sets first)
     int parts;                   // 0 all shells, 1 surface shell only, 2 medium shells only
+    const float4* pre_ray;       // nullable: primary pre-pass results, [n][V] (uniform ray sets)
+    const float* pre_Lo;         // [n][V][3]
 };
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -412,6 +414,37 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
         const int rec = s_rec;
         if (rec >= a.n) break;
         const int nb = a.n_bands ? a.n_bands[rec] : a.nb0;
+        if (a.n_bands && (nb < 2 || nb > a.nb0)) {
+            // a per-record band count outside [2, params n_bands] would overrun the shared
+            // buffers sized for params n_bands: the record is skipped and flagged
+            const vrc_records_view& o = a.out;
+            if (tid < 3) {
+                o.L[3 * rec + tid] = 0.f;
+                if (o.L_ss) o.L_ss[3 * rec + tid] = 0.f;
+                if (o.L_ms) o.L_ms[3 * rec + tid] = 0.f;
+                if (o.L_ff) o.L_ff[3 * rec + tid] = 0.f;
+            }
+            if (tid < 9) {
+                o.grad[9 * rec + tid] = 0.f;
+                if (o.grad_ss) o.grad_ss[9 * rec + tid] = 0.f;
+                if (o.grad_ms) o.grad_ms[9 * rec + tid] = 0.f;
+            }
+            if (tid < 18) {
+                o.hess[18 * rec + tid] = 0.f;
+                if (o.hess_ss) o.hess_ss[18 * rec + tid] = 0.f;
+                if (o.hess_ms) o.hess_ms[18 * rec + tid] = 0.f;
+            }
+            if (tid == 0 && o.kappa) o.kappa[rec] = 0.f;
+            if (tid < 3) o.pos[3 * rec + tid] = a.pos[3 * rec + tid];
+            if (tid == 0) {
+                o.status[rec] = VRC_REC_BAD_COUNT;
+                if (o.n_cells) o.n_cells[rec] = 0;
+                if (o.n_far) o.n_far[rec] = 0;
+                if (o.n_shells) o.n_shells[rec] = 0;
+            }
+            __syncthreads();
+            continue;
+        }
         const int ns = a.n_bands ? 2 * nb : a.ns0;
         const int N = nb * ns;
         const long long rid = a.rec_base + rec;
@@ -447,16 +480,28 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 } else {
                     gv = lv == PN ? N : N + 1;
                 }
-                float3 d = ray_direction_dev(a.seed, rid, gv, nb, ns);
-                float th;
-                int prim = bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
-                float3 Lo = f3(0.f, 0.f, 0.f);
+                float3 d, Lo = f3(0.f, 0.f, 0.f);
                 float te;
-                if (prim >= 0) {
-                    te = th;
-                    if (a.parts != 2) Lo = surface_radiance(sc, prim, x + d * te, d);
+                int prim = -1;
+                if (a.pre_ray) {
+                    // traced by k_primary: an escaped ray has zero radiance, so its Monte
+                    // Carlo term below adds an exact zero
+                    const size_t gi = (size_t)rec * (size_t)(N + 2) + gv;
+                    float4 rv = __ldg(&a.pre_ray[gi]);
+                    d = f3(rv.x, rv.y, rv.z);
+                    te = rv.w;
+                    Lo = f3(__ldg(&a.pre_Lo[3 * gi]), __ldg(&a.pre_Lo[3 * gi + 1]), __ldg(&a.pre_Lo[3 * gi + 2]));
+                    prim = 0;
                 } else {
-                    te = cube_exit_dev(x, d);
+                    d = ray_direction_dev(a.seed, rid, gv, nb, ns);
+                    float th;
+                    prim = bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
+                    if (prim >= 0) {
+                        te = th;
+                        if (a.parts != 2) Lo = surface_radiance(sc, prim, x + d * te, d);
+                    } else {
+                        te = cube_exit_dev(x, d);
+                    }
                 }
                 ray[lv] = make_float4(d.x, d.y, d.z, te);
                 Lr[lv] = Lo.x;
@@ -471,7 +516,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     neumaier(mc[1], mcc[1], w * Lo.y);
                     neumaier(mc[2], mcc[2], w * Lo.z);
                 }
-                if (a.out.hit_prim && (owned || (pole && ((lv == PN && north) || (lv == PS && south))))) {
+                if (a.out.hit_prim && !a.pre_ray && (owned || (pole && ((lv == PN && north) || (lv == PS && south))))) {
                     size_t o = (size_t)rec * a.out.dbg_stride + gv;
                     a.out.hit_prim[o] = prim;
                     a.out.hit_t[o] = te;
@@ -757,6 +802,53 @@ __global__ void k_radius(RecArgs a) {
                         o.radii ? o.radii + 3 * rec : nullptr, o.axes ? o.axes + 9 * rec : nullptr);
 }
 
+// Primary pre-pass for uniform ray sets: one thread per (record, ray), the closest hit and
+// the surface radiance with its shadow rays, written for the record kernel to load.  As a
+// flat launch it keeps every warp slot of the SM busy; inside the record kernel the same
+// traversal ran with two blocks per SM between barriers, at about half the rate.
+__global__ void __launch_bounds__(128) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
+    const long long V = (long long)a.nb0 * a.ns0 + 2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)a.n * V) return;
+    const int rec = (int)(i / V), gv = (int)(i - (long long)rec * V);
+    const float3 x = f3(a.pos[3 * rec], a.pos[3 * rec + 1], a.pos[3 * rec + 2]);
+    const float3 d = ray_direction_dev(a.seed, a.rec_base + rec, gv, a.nb0, a.ns0);
+    float th;
+    const int prim = bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
+    float3 Lo = f3(0.f, 0.f, 0.f);
+    float te;
+    if (prim >= 0) {
+        te = th;
+        if (a.parts != 2) Lo = surface_radiance(sc, prim, x + d * te, d);
+    } else {
+        te = cube_exit_dev(x, d);
+    }
+    ray[i] = make_float4(d.x, d.y, d.z, te);
+    Lo_out[3 * i] = Lo.x;
+    Lo_out[3 * i + 1] = Lo.y;
+    Lo_out[3 * i + 2] = Lo.z;
+    if (a.out.hit_prim) {
+        size_t o = (size_t)rec * a.out.dbg_stride + gv;
+        a.out.hit_prim[o] = prim;
+        a.out.hit_t[o] = te;
+    }
+}
+
+// The event quadruple for this launch when per-kernel timing is on (NULL otherwise, when
+// the stream is being captured into a graph, or when 64 launches are pending).
+static cudaEvent_t* timing_slot(vrc_scene* s, cudaStream_t st) {
+    if (!s->timing) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    if (s->n_timed >= 64) return nullptr;
+    if (s->n_timed >= s->t_ev_made) {
+        for (int e = 0; e < 4; ++e)
+            if (cudaEventCreate(&s->t_ev[s->n_timed][e]) != cudaSuccess) return nullptr;
+        s->t_ev_made = s->n_timed + 1;
+    }
+    return s->t_ev[s->n_timed++];
+}
+
 template <int NT>
 int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st) {
     auto kfn = k_records<NT>;
@@ -771,8 +863,18 @@ int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st)
     if (grid < 1) grid = 1;
     DevScene dv = s->dev;
     dv.use_lb = s->tuning.shadow_bvh ? 0 : 1;
+    cudaEvent_t* ev = timing_slot(s, st);
+    if (ev) cudaEventRecord(ev[0], st);
+    if (a.pre_ray) {
+        const long long rays = (long long)a.n * ((long long)a.nb0 * a.ns0 + 2);
+        k_primary<<<(unsigned)((rays + 127) / 128), 128, 0, st>>>(dv, a, const_cast<float4*>(a.pre_ray),
+                                                                   const_cast<float*>(a.pre_Lo));
+    }
+    if (ev) cudaEventRecord(ev[1], st);
     kfn<<<grid, NT, smem, st>>>(dv, a);
+    if (ev) cudaEventRecord(ev[2], st);
     k_radius<<<(a.n + 127) / 128, 128, 0, st>>>(a);
+    if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
@@ -810,10 +912,32 @@ static int ensure_order_scratch(vrc_scene* s, int n) {
     return VRC_OK;
 }
 
+// Primary pre-pass buffers for `rays` rays (uniform ray sets only; 28 B per ray).  Above
+// PRE_MAX_RAYS the record kernel traces its own primary rays instead.
+constexpr long long PRE_MAX_RAYS = 64ll << 20;   // 1.75 GB of buffers
+static int ensure_pre_scratch(vrc_scene* s, long long rays) {
+    if (s->pre_cap >= rays) return VRC_OK;
+    cudaFree(s->d_pre_ray);
+    cudaFree(s->d_pre_Lo);
+    s->d_pre_ray = nullptr;
+    s->d_pre_Lo = nullptr;
+    s->pre_cap = 0;
+    if (cudaMalloc((void**)&s->d_pre_ray, sizeof(float4) * (size_t)rays) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_pre_Lo, 3 * sizeof(float) * (size_t)rays) != cudaSuccess) {
+        cudaFree(s->d_pre_ray);
+        s->d_pre_ray = nullptr;
+        return VRC_ERR_OOM;
+    }
+    s->pre_cap = rays;
+    return VRC_OK;
+}
+
 extern "C" int vrc_set_record_tuning(vrc_scene* s, const vrc_record_tuning* t) {
     if (!s || !t) return VRC_ERR_INVALID;
     if (t->threads != 0 && t->threads != 128 && t->threads != 256 && t->threads != 512) return VRC_ERR_INVALID;
-    if (t->chunk_bands < 0 || t->blocks_per_sm < 0 || t->shadow_bvh < 0 || t->shadow_bvh > 1) return VRC_ERR_INVALID;
+    if (t->chunk_bands < 0 || t->blocks_per_sm < 0 || t->shadow_bvh < 0 || t->shadow_bvh > 1 || t->no_prepass < 0 ||
+        t->no_prepass > 1)
+        return VRC_ERR_INVALID;
     s->tuning = *t;
     return VRC_OK;
 }
@@ -821,6 +945,30 @@ extern "C" int vrc_set_record_tuning(vrc_scene* s, const vrc_record_tuning* t) {
 extern "C" int vrc_get_record_tuning(const vrc_scene* s, vrc_record_tuning* t) {
     if (!s || !t) return VRC_ERR_INVALID;
     *t = s->tuning;
+    return VRC_OK;
+}
+
+extern "C" int vrc_record_timing(vrc_scene* s, int32_t enable) {
+    if (!s || enable < 0 || enable > 1) return VRC_ERR_INVALID;
+    s->timing = enable;
+    s->n_timed = 0;
+    return VRC_OK;
+}
+
+extern "C" int vrc_record_kernel_times(vrc_scene* s, float* ms3, int32_t* launches) {
+    if (!s || !ms3) return VRC_ERR_INVALID;
+    ms3[0] = ms3[1] = ms3[2] = 0.f;
+    int n = s->n_timed;
+    for (int i = 0; i < n; ++i) {
+        if (cudaEventSynchronize(s->t_ev[i][3]) != cudaSuccess) return VRC_ERR_CUDA;
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s->t_ev[i][k], s->t_ev[i][k + 1]) != cudaSuccess) return VRC_ERR_CUDA;
+            ms3[k] += ms;
+        }
+    }
+    if (launches) *launches = n;
+    s->n_timed = 0;
     return VRC_OK;
 }
 
@@ -869,6 +1017,15 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.counter = s->d_counter;
     a.order = nullptr;
     a.parts = p->parts;
+    a.pre_ray = nullptr;
+    a.pre_Lo = nullptr;
+    if (!d_n_bands && !s->tuning.no_prepass) {
+        const long long rays = (long long)n * ((long long)nb * ns + 2);
+        if (rays <= PRE_MAX_RAYS && ensure_pre_scratch(s, rays) == VRC_OK) {
+            a.pre_ray = s->d_pre_ray;
+            a.pre_Lo = s->d_pre_Lo;
+        }
+    }
     VRC_CUDA_CHECK(cudaMemsetAsync(s->d_counter, 0, sizeof(int), st));
     if (d_n_bands && n > 1) {
         // largest ray sets first; the order and histogram live in scene-owned scratch
@@ -938,6 +1095,12 @@ extern "C" int vrc_records_graph_create(vrc_scene* s, const float* d_pos, int32_
     if (d_n_bands) {
         int rc = ensure_order_scratch(s, n);     // no allocation may happen inside the capture
         if (rc != VRC_OK) return rc;
+    } else if (!s->tuning.no_prepass) {
+        const long long rays = (long long)n * ((long long)p->n_bands * p->n_bins + 2);
+        if (rays <= PRE_MAX_RAYS) {
+            int rc = ensure_pre_scratch(s, rays);
+            if (rc != VRC_OK) return rc;
+        }
     }
     cudaStream_t cs;
     VRC_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1014,6 +1177,8 @@ extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n,
     VRC_CUDA_CHECK(cudaEventCreate(&e1));
     const int threads[3] = {128, 256, 512};
     const int chunks[4] = {0, 8, 16, 32};
+    const int n_pre = d_n_bands ? 1 : 2;     // uniform ray sets: with and without the pre-pass
+    for (int pi = 0; pi < n_pre; ++pi)
     for (int ti = 0; ti < 3; ++ti)
         for (int ci = 0; ci < 4; ++ci) {
             if (chunks[ci] >= p->n_bands) continue;
@@ -1021,6 +1186,7 @@ extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n,
             t.threads = threads[ti];
             t.chunk_bands = chunks[ci];
             t.blocks_per_sm = 0;
+            t.no_prepass = d_n_bands ? saved.no_prepass : pi;
             s->tuning = t;
             if (vrc_compute_records(s, d_pos, m, d_n_bands, p, out, stream) != VRC_OK) continue;
             cudaEventRecord(e0, st);

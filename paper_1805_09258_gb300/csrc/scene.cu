@@ -381,6 +381,10 @@ extern "C" void vrc_destroy_scene(vrc_scene* s) {
     cudaFree(s->d_prim);
     cudaFree(s->d_counter);
     cudaFree(s->d_order);
+    for (int i = 0; i < s->t_ev_made; ++i)
+        for (int e = 0; e < 4; ++e) cudaEventDestroy(s->t_ev[i][e]);
+    cudaFree(s->d_pre_ray);
+    cudaFree(s->d_pre_Lo);
     cudaFree(s->h_stage_dev);
     for (int l = 0; l < VRC_MAX_LIGHTS; ++l) {
         cudaFree(s->d_lb_start[l]);

@@ -56,6 +56,15 @@ struct vrc_scene {
     int* d_counter;       // persistent-launch work counter (one int)
     int* d_order;         // largest-first record order + histogram (grown on demand)
     int order_cap;
+    // per-kernel timing of record launches (vrc_record_kernel_times): event triples, one
+    // per launch since the last read; recorded only while enabled and not capturing
+    int timing;
+    int n_timed;
+    cudaEvent_t t_ev[64][4];
+    int t_ev_made;
+    float4* d_pre_ray;    // primary pre-pass: (direction, t_end) per ray (grown on demand)
+    float* d_pre_Lo;      // primary pre-pass: surface radiance rgb per ray
+    long long pre_cap;    // rays the pre-pass buffers hold
     // device staging for vrc_compute_records_host (grown on demand)
     float* h_stage_dev;
     size_t h_stage_floats;

@@ -208,3 +208,22 @@ def test_single_and_multiple_scattering_parts(vrc):
     invalid = W.configs.replace(w.params, parts=3)
     with pytest.raises(vrc.VrcError):
         run_gpu(vrc, w.scene, invalid, pos[:2])
+
+
+def test_out_of_range_band_counts_are_flagged_not_computed(vrc):
+    """A per-record band count outside [2, params n_bands] would overrun the shared buffers
+    sized for params n_bands: such records are skipped with status VRC_REC_BAD_COUNT while
+    the others are computed as usual."""
+    w = W.config1()
+    pos = w.positions(6, seed=17)
+    p = RecordParams(n_bands=8, n_bins=16)
+    nb = np.array([4, 9, 1, 8, 0, 6], np.int32)          # 9 > 8, 1 < 2, 0 < 2: bad
+    g = run_gpu(vrc, w.scene, p, pos, n_bands=nb)
+    bad = np.array([False, True, True, False, True, False])
+    assert np.all((g["status"][bad] & 16) != 0) and np.all((g["status"][~bad] & 16) == 0)
+    assert np.all(g["L"][bad] == 0) and np.all(g["hess"][bad] == 0)
+    good = np.flatnonzero(~bad)
+    for i in good:
+        one = run_gpu(vrc, w.scene, W.configs.replace(p, n_bands=int(nb[i]), n_bins=2 * int(nb[i]), rec_base=int(i)),
+                      pos[i:i + 1])
+        assert np.array_equal(g["L"][i], one["L"][0]) and np.array_equal(g["hess"][i], one["hess"][0])

@@ -6,7 +6,7 @@
 | mid (config2) | 170 random boxes + ground, 2,048 tris | 4,096 | 32 x 64 | 1M |
 | batching (config3) | 8,333 boxes + ground, 100,000 tris | 100,000 | 8x16 .. 64x128 log-uniform | - |
 | learned (config4) | 16 mid-style scenes | training set | 32 x 64 (+ coarse 8 x 16) | - |
-| render (config5) | 20,833 boxes + ground, 250,000 tris | adaptive | 32 x 64 | 1920x1080x64 |
+| render (config5) | 170 tessellated boxes + ground grid, 250,040 tris | adaptive | 32 x 64 | 1920x1080x64 |
 
 Common settings: medium fills the unit cube, one point light at (0.5, 0.5, 0.92)
 with RGB intensity (1.0, 0.9, 0.8), Lambertian surfaces of albedo 0.7, march
@@ -20,8 +20,8 @@ from typing import Optional
 
 import numpy as np
 
-from .scenes import (Medium, PointLight, Scene, box_triangles, cube_walls, ground_quads,
-                     inside_any_box, random_boxes)
+from .scenes import (Medium, PointLight, Scene, box_triangles, box_triangles_tessellated, cube_walls, ground_grid,
+                     ground_quads, inside_any_box, random_boxes)
 
 SEED_SCENE, SEED_RECORDS, SEED_JITTER, SEED_QUERIES = 1, 2, 3, 4
 LIGHT_POS = (0.5, 0.5, 0.92)
@@ -154,14 +154,23 @@ def config4(scene_seed: int = SEED_SCENE) -> Workload:
 
 
 def render_scene(seed: int = SEED_SCENE) -> Scene:
-    """20,833 boxes (sides log-uniform in [0.003, 0.016], box optical depth about 2.3 per
-    unit length, as in the batching scene) + ground: 250,000 triangles."""
-    return _box_scene("20,833 boxes + ground (250,000 tris)", 20833, 0.003, 0.016, True, 4,
-                      Medium(0.4, 0.1, 0.7), seed)
+    """170 boxes with sides U[0.02, 0.2] (the mid scene's distribution), every face
+    tessellated into 11 x 11 quads, plus a 40 x 40 ground grid: 250,040 triangles.
+    Boxes of this size cast shadows that a 32 x 64-ray record resolves; a field of
+    thousands of millimetre boxes (tried first) gives radiance whose shadow structure is
+    finer than the record's ray set, so no tolerance changes the frame's error."""
+    rng = np.random.default_rng(seed)
+    boxes = random_boxes(rng, 170, 0.02, 0.2, False, keep_clear=[np.array(LIGHT_POS, np.float64)],
+                         clear_radius=0.02)
+    tris = np.concatenate([box_triangles_tessellated(b[0], b[1], 11) for b in boxes] + [ground_grid(40)])
+    tris = np.ascontiguousarray(tris, dtype=np.float32)
+    albedo = np.full((tris.shape[0], 3), SURFACE_ALBEDO, np.float32)
+    return Scene(tris=tris, albedo=albedo, medium=Medium(0.4, 0.1, 0.7), lights=[PointLight(LIGHT_POS, LIGHT_I)],
+                 boxes=boxes, name="170 tessellated boxes + ground grid (250,040 tris)")
 
 
 def config5() -> Workload:
-    """Render-shaped workload: 250,000 triangles, 1920x1080 camera, 64 march steps."""
+    """Render-shaped workload: 250,040 triangles, 1920x1080 camera, 64 march steps."""
     scene = render_scene()
     return Workload("render: 250k tris, 1920x1080x64 march points", scene,
                     RecordParams(n_bands=32, n_bins=64, omega_o=(0.0, -1.0, 0.0)),

@@ -74,6 +74,42 @@ def box_triangles(lo, hi) -> np.ndarray:
     return np.stack([c[list(f)] for f in faces]).astype(np.float32)
 
 
+def box_triangles_tessellated(lo, hi, n: int) -> np.ndarray:
+    """An axis-aligned box with every face split into an n x n grid of quads (2 triangles
+    each): 12 n^2 triangles, normals outward."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    out = []
+    for ax in range(3):
+        u, v = [a for a in range(3) if a != ax]
+        for side in (0, 1):
+            g = np.linspace(0.0, 1.0, n + 1)
+            P = np.zeros((n + 1, n + 1, 3))
+            P[..., ax] = hi[ax] if side else lo[ax]
+            P[..., u] = lo[u] + (hi[u] - lo[u]) * g[:, None]
+            P[..., v] = lo[v] + (hi[v] - lo[v]) * g[None, :]
+            a, b, c, d = P[:-1, :-1], P[1:, :-1], P[1:, 1:], P[:-1, 1:]
+            t1 = np.stack([a, b, c], axis=2).reshape(-1, 3, 3)
+            t2 = np.stack([a, c, d], axis=2).reshape(-1, 3, 3)
+            tri = np.concatenate([t1, t2])
+            # wind outward: the normal must point along +ax on the hi side, -ax on the lo side
+            nrm = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])[:, ax]
+            flip = (nrm < 0) if side else (nrm > 0)
+            tri[flip] = tri[flip][:, [0, 2, 1]]
+            out.append(tri)
+    return np.concatenate(out).astype(np.float32)
+
+
+def ground_grid(m: int) -> np.ndarray:
+    """Ground plane z = 0 over [0,1]^2 as an m x m grid of quads (2 m^2 triangles)."""
+    g = np.linspace(0.0, 1.0, m + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    P = np.stack([X, Y, np.zeros_like(X)], axis=-1)
+    a, b, c, d = P[:-1, :-1], P[1:, :-1], P[1:, 1:], P[:-1, 1:]
+    return np.concatenate([np.stack([a, b, c], 2).reshape(-1, 3, 3),
+                           np.stack([a, c, d], 2).reshape(-1, 3, 3)]).astype(np.float32)
+
+
 def cube_walls() -> np.ndarray:
     """The six faces of the unit cube as 12 triangles (the room of the small workload)."""
     return box_triangles((0, 0, 0), (1, 1, 1))
