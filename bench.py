@@ -482,7 +482,7 @@ def run_render(args, w):
         wsc = W.configs.render_scene(seed)
         exs.add(vrc.Scene.from_workload(wsc), W.record_positions(wsc, 16384, seed + 50), rp, coarse)
     mlp = vrc.MLP(M.init_params(5))
-    F, T = exs.view()
+    F, T = exs.view(shuffle=True)
     learned.train(mlp, F, T, steps=1500, batch=4096, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0

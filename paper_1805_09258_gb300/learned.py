@@ -3,9 +3,10 @@
 Targets are the method's own output: log R of full records computed by
 vrc_compute_records; inputs are the coarse features of the same positions
 (vrc_coarse_features).  Training runs the library's tensor-core gradient kernel and
-AdamW (vrc_mlp_train_step) over contiguous mini-batches.  The record positions are drawn
-uniformly at random, so consecutive examples are already in random order.  This module
-only sequences library calls; examples are written into caller-sized slices.
+AdamW (vrc_mlp_train_step) over contiguous mini-batches.  Within a scene the record
+positions are drawn uniformly at random; view(shuffle=True) also interleaves the scenes
+(one seeded permutation of the rows), so no mini-batch comes from a single scene.  This
+module only sequences library calls; examples are written into caller-sized slices.
 """
 from __future__ import annotations
 
@@ -36,8 +37,14 @@ class ExampleSet:
         coarse_features(scene, pos, coarse_params, out=self.feat[self.n:self.n + m])
         self.n += m
 
-    def view(self):
-        return self.feat[:self.n], self.logr[:self.n]
+    def view(self, shuffle: bool = False, seed: int = 0):
+        if not shuffle:
+            return self.feat[:self.n], self.logr[:self.n]
+        torch = _torch()
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed)
+        perm = torch.randperm(self.n, generator=g, device="cuda")
+        return self.feat[:self.n][perm].contiguous(), self.logr[:self.n][perm].contiguous()
 
 
 def train(mlp: MLP, feat, target, steps: int, batch: int = 4096, lr: float = 2e-3, weight_decay: float = 1e-4,

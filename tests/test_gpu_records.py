@@ -227,3 +227,20 @@ def test_out_of_range_band_counts_are_flagged_not_computed(vrc):
         one = run_gpu(vrc, w.scene, W.configs.replace(p, n_bands=int(nb[i]), n_bins=2 * int(nb[i]), rec_base=int(i)),
                       pos[i:i + 1])
         assert np.array_equal(g["L"][i], one["L"][0]) and np.array_equal(g["hess"][i], one["hess"][0])
+
+
+def test_prepass_matches_in_kernel_tracing(vrc):
+    """The primary-ray pre-pass (a flat kernel that traces ahead of the record kernel) gives
+    the records the record kernel computes when it traces its own primary rays."""
+    w = W.config2()
+    pos = w.positions(300, seed=23)
+    a = run_gpu(vrc, w.scene, w.params, pos)
+    b = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(no_prepass=1))
+    for k in ("L", "grad", "hess", "radius"):
+        x, y = a[k].astype(np.float64), b[k].astype(np.float64)
+        assert np.max(np.abs(x - y)) <= 1e-6 * np.abs(y).max() + 1e-12, k
+    assert np.array_equal(a["n_cells"], b["n_cells"])
+    # debug hit ids are written by the pre-pass in the same layout
+    a = run_gpu(vrc, w.scene, w.params, pos[:8], debug_hits=True)
+    b = run_gpu(vrc, w.scene, w.params, pos[:8], debug_hits=True, tuning=dict(no_prepass=1))
+    assert np.array_equal(a["hit_prim"], b["hit_prim"]) and np.array_equal(a["hit_t"], b["hit_t"])
