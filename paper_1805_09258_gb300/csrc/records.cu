@@ -42,8 +42,11 @@ struct RecArgs {
     int* counter;                // work counter (reset before the launch)
     const int* order;            // nullable: work item -> record (largest ray sets first)
     int parts;                   // 0 all shells, 1 surface shell only, 2 medium shells only
-    const float4* pre_ray;       // nullable: primary pre-pass results, [n][V] (uniform ray sets)
-    const float* pre_Lo;         // [n][V][3]
+    const float4* pre_ray;       // nullable: primary pre-pass results of the current batch,
+                                 // [item - item_base][pre_stride]
+    const float* pre_Lo;         // [item - item_base][pre_stride][3]
+    int pre_stride;              // rays per pre-pass slot (the largest ray set of the launch)
+    int item_base, item_end;     // work items of the current batch (positions in `order`)
 };
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -403,16 +406,18 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
     unsigned* litm = reinterpret_cast<unsigned*>(wq + NW * 64);   // [2][LW]: vertex has radiance (bit per vertex)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float sigma_t = sc.sigma_t, g = sc.g;
-    __shared__ int s_rec;
+    __shared__ int s_rec, s_item;
 
     for (;;) {
         if (tid == 0) {
-            int item = atomicAdd(a.counter, 1);
-            s_rec = item < a.n ? (a.order ? a.order[item] : item) : a.n;
+            int item = a.item_base + atomicAdd(a.counter, 1);
+            s_item = item;
+            s_rec = item < a.item_end ? (a.order ? a.order[item] : item) : a.n;
         }
         __syncthreads();
         const int rec = s_rec;
         if (rec >= a.n) break;
+        const int slot = s_item - a.item_base;           // pre-pass slot of this record
         const int nb = a.n_bands ? a.n_bands[rec] : a.nb0;
         if (a.n_bands && (nb < 2 || nb > a.nb0)) {
             // a per-record band count outside [2, params n_bands] would overrun the shared
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 if (a.pre_ray) {
                     // traced by k_primary: an escaped ray has zero radiance, so its Monte
                     // Carlo term below adds an exact zero
-                    const size_t gi = (size_t)rec * (size_t)(N + 2) + gv;
+                    const size_t gi = (size_t)slot * (size_t)a.pre_stride + gv;
                     float4 rv = __ldg(&a.pre_ray[gi]);
                     d = f3(rv.x, rv.y, rv.z);
                     te = rv.w;
@@ -802,17 +807,23 @@ __global__ void k_radius(RecArgs a) {
                         o.radii ? o.radii + 3 * rec : nullptr, o.axes ? o.axes + 9 * rec : nullptr);
 }
 
-// Primary pre-pass for uniform ray sets: one thread per (record, ray), the closest hit and
-// the surface radiance with its shadow rays, written for the record kernel to load.  As a
-// flat launch it keeps every warp slot of the SM busy; inside the record kernel the same
-// traversal ran with two blocks per SM between barriers, at about half the rate.
+// Primary pre-pass: one thread per (work item, ray) of the current batch, the closest hit
+// and the surface radiance with its shadow rays, written for the record kernel to load.
+// As a flat launch it keeps every warp slot of the SM busy; inside the record kernel the
+// same traversal ran with two blocks per SM between barriers, at about half the rate.
+// Slots are pre_stride rays wide; a smaller ray set leaves the rest of its slot unused.
 __global__ void __launch_bounds__(128) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
-    const long long V = (long long)a.nb0 * a.ns0 + 2;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)a.n * V) return;
-    const int rec = (int)(i / V), gv = (int)(i - (long long)rec * V);
+    const int slot = (int)(i / a.pre_stride), gv = (int)(i - (long long)slot * a.pre_stride);
+    const int item = a.item_base + slot;
+    if (item >= a.item_end) return;
+    const int rec = a.order ? a.order[item] : item;
+    const int nb = a.n_bands ? a.n_bands[rec] : a.nb0;
+    if (a.n_bands && (nb < 2 || nb > a.nb0)) return;        // flagged by the record kernel
+    const int ns = a.n_bands ? 2 * nb : a.ns0;
+    if (gv >= nb * ns + 2) return;
     const float3 x = f3(a.pos[3 * rec], a.pos[3 * rec + 1], a.pos[3 * rec + 2]);
-    const float3 d = ray_direction_dev(a.seed, a.rec_base + rec, gv, a.nb0, a.ns0);
+    const float3 d = ray_direction_dev(a.seed, a.rec_base + rec, gv, nb, ns);
     float th;
     const int prim = bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
     float3 Lo = f3(0.f, 0.f, 0.f);
@@ -849,8 +860,14 @@ static cudaEvent_t* timing_slot(vrc_scene* s, cudaStream_t st) {
     return s->t_ev[s->n_timed++];
 }
 
+// Records per pre-pass batch: the pre-pass buffers hold `cap` rays of `stride`-ray slots.
+static int batch_records(long long cap, int stride, int n) {
+    long long b = cap / stride;
+    return (int)(b < 1 ? 1 : (b > n ? n : b));
+}
+
 template <int NT>
-int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st) {
+int launch_records(vrc_scene* s, const RecArgs& a0, size_t smem, cudaStream_t st) {
     auto kfn = k_records<NT>;
     if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return VRC_ERR_UNSUPPORTED;
@@ -858,20 +875,30 @@ int launch_records(vrc_scene* s, const RecArgs& a, size_t smem, cudaStream_t st)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, smem) != cudaSuccess || per_sm < 1)
         return VRC_ERR_UNSUPPORTED;
     if (s->tuning.blocks_per_sm > 0 && s->tuning.blocks_per_sm < per_sm) per_sm = s->tuning.blocks_per_sm;
-    int grid = per_sm * s->sm_count;
-    if (grid > a.n) grid = a.n;
-    if (grid < 1) grid = 1;
     DevScene dv = s->dev;
     dv.use_lb = s->tuning.shadow_bvh ? 0 : 1;
-    cudaEvent_t* ev = timing_slot(s, st);
+    RecArgs a = a0;
+    // batches of work items (in `order` when given) whose ray sets fit the pre-pass buffers
+    const int B = a.pre_ray ? batch_records(s->pre_cap, a.pre_stride, a.n) : a.n;
+    const int n_batches = (a.n + B - 1) / B;
+    cudaEvent_t* ev = n_batches == 1 ? timing_slot(s, st) : nullptr;
     if (ev) cudaEventRecord(ev[0], st);
-    if (a.pre_ray) {
-        const long long rays = (long long)a.n * ((long long)a.nb0 * a.ns0 + 2);
-        k_primary<<<(unsigned)((rays + 127) / 128), 128, 0, st>>>(dv, a, const_cast<float4*>(a.pre_ray),
-                                                                   const_cast<float*>(a.pre_Lo));
+    for (int b0 = 0; b0 < a.n; b0 += B) {
+        a.item_base = b0;
+        a.item_end = b0 + B < a.n ? b0 + B : a.n;
+        const int nb_items = a.item_end - a.item_base;
+        if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), st) != cudaSuccess) return VRC_ERR_CUDA;
+        if (a.pre_ray) {
+            const long long rays = (long long)nb_items * a.pre_stride;
+            k_primary<<<(unsigned)((rays + 127) / 128), 128, 0, st>>>(dv, a, const_cast<float4*>(a.pre_ray),
+                                                                       const_cast<float*>(a.pre_Lo));
+        }
+        if (ev) cudaEventRecord(ev[1], st);
+        int grid = per_sm * s->sm_count;
+        if (grid > nb_items) grid = nb_items;
+        if (grid < 1) grid = 1;
+        kfn<<<grid, NT, smem, st>>>(dv, a);
     }
-    if (ev) cudaEventRecord(ev[1], st);
-    kfn<<<grid, NT, smem, st>>>(dv, a);
     if (ev) cudaEventRecord(ev[2], st);
     k_radius<<<(a.n + 127) / 128, 128, 0, st>>>(a);
     if (ev) cudaEventRecord(ev[3], st);
@@ -912,8 +939,8 @@ static int ensure_order_scratch(vrc_scene* s, int n) {
     return VRC_OK;
 }
 
-// Primary pre-pass buffers for `rays` rays (uniform ray sets only; 28 B per ray).  Above
-// PRE_MAX_RAYS the record kernel traces its own primary rays instead.
+// Primary pre-pass buffers for `rays` rays (28 B per ray), at most PRE_MAX_RAYS: larger
+// launches run in batches of work items whose slots fit.
 constexpr long long PRE_MAX_RAYS = 64ll << 20;   // 1.75 GB of buffers
 static int ensure_pre_scratch(vrc_scene* s, long long rays) {
     if (s->pre_cap >= rays) return VRC_OK;
@@ -1019,14 +1046,18 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.parts = p->parts;
     a.pre_ray = nullptr;
     a.pre_Lo = nullptr;
-    if (!d_n_bands && !s->tuning.no_prepass) {
-        const long long rays = (long long)n * ((long long)nb * ns + 2);
-        if (rays <= PRE_MAX_RAYS && ensure_pre_scratch(s, rays) == VRC_OK) {
+    a.pre_stride = nb * ns + 2;                       // the largest ray set of the launch
+    a.item_base = 0;
+    a.item_end = n;
+    if (!s->tuning.no_prepass) {
+        long long rays = (long long)n * a.pre_stride;
+        if (rays > PRE_MAX_RAYS) rays = PRE_MAX_RAYS / a.pre_stride * a.pre_stride;
+        if (rays < a.pre_stride) rays = a.pre_stride;
+        if (ensure_pre_scratch(s, rays) == VRC_OK) {
             a.pre_ray = s->d_pre_ray;
             a.pre_Lo = s->d_pre_Lo;
         }
     }
-    VRC_CUDA_CHECK(cudaMemsetAsync(s->d_counter, 0, sizeof(int), st));
     if (d_n_bands && n > 1) {
         // largest ray sets first; the order and histogram live in scene-owned scratch
         int rc = ensure_order_scratch(s, n);
@@ -1095,12 +1126,14 @@ extern "C" int vrc_records_graph_create(vrc_scene* s, const float* d_pos, int32_
     if (d_n_bands) {
         int rc = ensure_order_scratch(s, n);     // no allocation may happen inside the capture
         if (rc != VRC_OK) return rc;
-    } else if (!s->tuning.no_prepass) {
-        const long long rays = (long long)n * ((long long)p->n_bands * p->n_bins + 2);
-        if (rays <= PRE_MAX_RAYS) {
-            int rc = ensure_pre_scratch(s, rays);
-            if (rc != VRC_OK) return rc;
-        }
+    }
+    if (!s->tuning.no_prepass) {
+        const long long stride = d_n_bands ? 2ll * p->n_bands * p->n_bands + 2 : (long long)p->n_bands * p->n_bins + 2;
+        long long rays = (long long)n * stride;
+        if (rays > PRE_MAX_RAYS) rays = PRE_MAX_RAYS / stride * stride;
+        if (rays < stride) rays = stride;
+        int rc = ensure_pre_scratch(s, rays);
+        if (rc != VRC_OK) return rc;
     }
     cudaStream_t cs;
     VRC_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1177,7 +1210,7 @@ extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n,
     VRC_CUDA_CHECK(cudaEventCreate(&e1));
     const int threads[3] = {128, 256, 512};
     const int chunks[4] = {0, 8, 16, 32};
-    const int n_pre = d_n_bands ? 1 : 2;     // uniform ray sets: with and without the pre-pass
+    const int n_pre = 2;                      // with and without the primary pre-pass
     for (int pi = 0; pi < n_pre; ++pi)
     for (int ti = 0; ti < 3; ++ti)
         for (int ci = 0; ci < 4; ++ci) {
@@ -1186,7 +1219,7 @@ extern "C" int vrc_autotune_records(vrc_scene* s, const float* d_pos, int32_t n,
             t.threads = threads[ti];
             t.chunk_bands = chunks[ci];
             t.blocks_per_sm = 0;
-            t.no_prepass = d_n_bands ? saved.no_prepass : pi;
+            t.no_prepass = pi;
             s->tuning = t;
             if (vrc_compute_records(s, d_pos, m, d_n_bands, p, out, stream) != VRC_OK) continue;
             cudaEventRecord(e0, st);
