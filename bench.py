@@ -165,7 +165,7 @@ def run_reference(args, w, rank, world):
     value = w.n_records / t_step
     sample = (f"{n_rec} records of the {w.n_records}-record batch on {threads} threads and {n_q} of the "
               f"{w.n_queries} queries (brute force, 1 thread) per step; full-step time extrapolated per unit")
-    line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "records": w.n_records, "rays_per_record": w.params.n_rays,

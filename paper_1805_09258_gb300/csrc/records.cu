@@ -385,6 +385,9 @@ __device__ __noinline__ void write_ellipsoid(const double h[6], const double lam
 // Registers are capped at 128 per thread (2 blocks of 256 per SM): the traversal phases
 // are latency-bound and need the warps; a lower cap (85) spills the cell math and was
 // slower, an uncapped build took more registers and left one block per SM.
+#ifndef VRC_MERGE_LEFTOVERS
+#define VRC_MERGE_LEFTOVERS 1
+#endif
 #ifndef VRC_RECORDS_REGS
 #define VRC_RECORDS_REGS 128
 #endif
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
     int* wq = misc + 4;                                      // [NW][64] lit-cell queues
     const int LW = (a.cap + 31) >> 5;
     unsigned* litm = reinterpret_cast<unsigned*>(wq + NW * 64);   // [2][LW]: vertex has radiance (bit per vertex)
+    int* wcnt = reinterpret_cast<int*>(litm + 2 * LW);            // [NW] leftover lit cells per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float sigma_t = sc.sigma_t, g = sc.g;
     __shared__ int s_rec, s_item;
@@ -668,10 +672,31 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         qn -= 32;
                     }
                 }
+#if VRC_MERGE_LEFTOVERS
+                // the warps' leftover lit cells (fewer than 32 each) of this shell: published,
+                // then processed as one warp-major list, a full chunk of 32 per warp, instead
+                // of one partly idle call per warp (the order is fixed: results stay
+                // deterministic)
+                if (lane == 0) wcnt[warp] = qn;
+                __syncthreads();
+                {
+                    int tot = 0, src = -1;
+                    const int t = warp * 32 + lane;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        const int cw = wcnt[w];
+                        if (src < 0 && t >= tot && t < tot + cw) src = wq[w * 64 + (t - tot)];
+                        tot += cw;
+                    }
+                    if (warp * 32 < tot) process(src);      // src -1: an idle lane
+                    __syncwarp();
+                }
+#else
                 if (qn > 0) {
                     process(lane < qn ? wqw[lane] : -1);
                     __syncwarp();
                 }
+#endif
                 __syncthreads();
             }
         }
@@ -764,7 +789,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
 size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
     return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
-           (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32) * 4;
+           (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32) * 4 + (size_t)nw * 4;
 }
 
 // Radius stage, one thread per record after the record kernel (its FP64 work would
