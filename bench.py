@@ -37,7 +37,7 @@ METRIC = "records/s (L_i+grad+Hessian) and queries/s at stated oracle error; lea
 # exp and atan2 = 1), counted from cell_eval's source for the anisotropic path (g != 0):
 # solid angle and derivatives 318, phase function and derivatives 135, the accumulation
 # adds 30 and the Hessian norm 14, plus 213 per tied furthest vertex (transmittance,
-# product rule, RGB scatter).  See DESIGN.md, "Record kernel roofline".
+# product rule, RGB scatter).
 FLOP_CELL_BASE = 318 + 135 + 30 + 14
 FLOP_PER_FAR_VERTEX = 213
 
@@ -113,6 +113,11 @@ def measured_peaks():
         except (OSError, ValueError):
             pass
     return None
+
+
+# DRAM bytes per record of k_records (the pre-pass rays it loads dominate), from one ncu
+# capture of a 1,024-record launch of the mid workload: (60.13 MB + 0.14 MB) / 1,024
+K_RECORDS_DRAM_BYTES_PER_RECORD = (60.132608e6 + 0.14336e6) / 1024
 
 
 def fp32_peak_tflops(sm_mhz: float = 2070.0) -> float:
@@ -331,7 +336,10 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                 "queries_per_s_kernel": w.n_queries / (q_ms * 1e-3),
                 "roofline": {"kernel": "k_records", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                              "launch_ms": kernel_ms[1],
-                             "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                             "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                             "traffic": K_RECORDS_DRAM_BYTES_PER_RECORD * w.n_records,
+                             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1,024-record "
+                                               "launch of this workload, scaled by records",
                              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                              "lit_cells_per_launch": int(n_cells.sum()), "far_vertex_evals": int(n_far.sum()),
                              "flop_per_launch": flop},
