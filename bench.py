@@ -319,6 +319,8 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
         peaks = measured_peaks()
         fp32_peak = fp32_peak_tflops(2070.0)
         flop = flop_per_launch(n_cells, n_far)
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0)) if peaks else 6800.0
+        q_gbs = (28.0 * w.n_queries + 64.0 * w.n_records) / (q_ms * 1e-3) / 1e9
         # the cell arithmetic runs in k_records alone: its own launch duration (library-side
         # CUDA events on the launching stream, averaged over the timed steps)
         achieved = flop / (kernel_ms[1] * 1e-3) / 1e12
@@ -343,6 +345,11 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                              "lit_cells_per_launch": int(n_cells.sum()), "far_vertex_evals": int(n_far.sum()),
                              "flop_per_launch": flop},
+                "query_roofline": {"kernel": "k_query", "bound": "hbm", "achieved": q_gbs, "peak": hbm_peak,
+                                   "frac": q_gbs / hbm_peak, "unit": "GB/s",
+                                   "note": "algorithmic 28 B per query + 64 B per record row; the kernel is bound "
+                                           "by its candidate tests, not by HBM"},
+                "primary_rays_per_s": w.n_records * w.params.n_rays / (kernel_ms[0] * 1e-3),
                 "clocks": clk,
                 "e2e": None if math.isnan(e2e_s) else
                 {"value": world * w.n_records / e2e_s, "unit": "records/s", "h2d_bytes_per_step": int(h2d),
@@ -462,6 +469,69 @@ def run_flat(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp(args):
+    """Extra measurement (not the default line): the learned radius predictor's kernels.
+    Inference: 1M feature rows (256 float32 each) -> log radius; a pass reads 1,028 B per
+    row, so its roofline is HBM (41,088 FLOP per row on the tensor pipe: 40 FLOP/B).
+    Training: AdamW steps on 4,096-row batches (forward + backward, about 3 x the forward
+    FLOP per row), a latency-bound chain of small launches."""
+    import torch
+    import oracle.mlp as M
+    import paper_1805_09258_gb300 as vrc
+    from paper_1805_09258_gb300 import build as vbuild
+    vbuild.build()
+    n = 1 << 20
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    feat = torch.randn((n, 256), generator=g, device="cuda") * 0.5 - 1.0
+    tgt = torch.randn((n,), generator=g, device="cuda") * 0.4 - 1.8
+    out = torch.empty((n,), device="cuda")
+    flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device="cuda")
+    mlp = vrc.MLP(M.init_params(5))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        mlp.predict(feat, out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mlp.predict(feat, out)
+        e1.record(stream)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b in ts]))
+    bsz, n_steps = 4096, 200
+    for s_ in range(args.warmup):
+        mlp.train_step(feat[:bsz], tgt[:bsz], 1e-3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in range(n_steps):
+        lo = (s_ * bsz) % (n - bsz)
+        mlp.train_step(feat[lo:lo + bsz], tgt[lo:lo + bsz], 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / n_steps
+    peaks = measured_peaks() or {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    bytes_row, flop_row = 256 * 4 + 4, 2 * (256 * 64 + 64 * 64 + 64)
+    fwd_gbs = n * bytes_row / (fwd_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": n / (fwd_ms * 1e-3), "unit": "radius predictions/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd_ms, "higher_is_better": True,
+            "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": "learned radius predictor: 256-64-64-1 GELU MLP, 1M rows; training batches of 4,096",
+                       "l2": "flushed between timed passes (256 MB write)"},
+            "roofline": {"kernel": "k_mlp_forward", "bound": "hbm", "achieved": fwd_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": fwd_gbs / hbm, "traffic": None,
+                         "tensor_tflops": n * flop_row / (fwd_ms * 1e-3) / 1e12, "bf16_peak_tflops": bf16},
+            "train_step_ms": step_ms, "train_rows_per_s": bsz / (step_ms * 1e-3),
+            "train_tflops": 3 * flop_row * bsz / (step_ms * 1e-3) / 1e12}
+    print(json.dumps(line), flush=True)
+
+
 def run_render(args, w):
     """Extra measurement (not the default line): one 1920x1080 frame of the render-shaped
     workload, plain vs learned placement (and ellipsoidal / split-cache variants), each at
@@ -546,7 +616,8 @@ def run_render(args, w):
         fr = render_frame(scene, cam, rpe, **kw)
         im = fr.image.cpu().numpy().reshape(Hd, Wd, 3)
         img = np.concatenate([im[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3) for (x0, y0) in crops])
-        res[name] = {"frame_ms": fr.seconds * 1e3, "records": fr.n_records, "rel_rmse": rel_rmse(img),
+        res[name] = {"frame_ms": fr.seconds * 1e3, "placement_ms": fr.placement_s * 1e3, "records": fr.n_records,
+                     "rel_rmse": rel_rmse(img),
                      "eps": eps, "passes": len(fr.passes), "misses_repaired": fr.misses,
                      "records_ss_ms": None if fr.placement2 is None else [fr.placement.n_records,
                                                                           fr.placement2.n_records]}
@@ -599,14 +670,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat"],
-                    help="mid (the default line), or the batching, render or 2D workload (extra measurements)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat", "mlp"],
+                    help="mid (the default line), or the batching, render, 2D or MLP workload (extra measurements)")
     args = ap.parse_args()
     if args.workload == "batching":
         run_batching(args, W.config3())
         return
     if args.workload == "render":
         run_render(args, W.config5())
+        return
+    if args.workload == "mlp":
+        run_mlp(args)
         return
     if args.workload == "flat":
         from workloads import flat

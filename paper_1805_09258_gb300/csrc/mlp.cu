@@ -198,6 +198,36 @@ __device__ void stage_rows(unsigned char* base, const float* src, int rows, int 
     }
 }
 
+// The same for a [rows x K] tile streamed from HBM: each thread issues the loads of 8 chunks
+// before converting any of them, so 8x more bytes are in flight per thread.
+__device__ void stage_rows_stream(unsigned char* base, const float* src, int rows, int valid_rows, int K, int ld) {
+    const int cpr = K / 8, chunks = rows * cpr;
+    for (int q0 = threadIdx.x; q0 < chunks; q0 += 8 * blockDim.x) {
+        float4 a[8], b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * blockDim.x;
+            const int row = q / cpr, k0 = (q - row * cpr) * 8;
+            if (q < chunks && row < valid_rows) {
+                const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)row * ld + k0);
+                a[u] = __ldcs(s4);
+                b[u] = __ldcs(s4 + 1);
+            } else {
+                a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                b[u] = a[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * blockDim.x;
+            if (q >= chunks) break;
+            const int row = q / cpr, k0 = (q - row * cpr) * 8;
+            const float v[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
+            st_chunk(base, row, k0, rows, v);
+        }
+    }
+}
+
 // sum of v over the block's 128 threads, in a fixed order (warp butterfly, then warps 0..3)
 __device__ __forceinline__ float block_sum_fixed(float v, float* scratch4) {
 #pragma unroll
@@ -222,7 +252,10 @@ struct MlpSmem {
     static constexpr uint32_t DZ2T = DZ2 + 16384;          // 64 x 128 (16 KB)
     static constexpr uint32_t DZ1T = DZ2T + 16384;         // 64 x 128 (16 KB)
     static constexpr uint32_t END = DZ1T + 16384;          // 212,992
-    static constexpr uint32_t FWD_END = H1 + 16384;        // forward kernel: X, W1, W2, (W2T), H1
+    // forward kernel: X, W1, W2; its H1 reuses X once the first product has read it, so two
+    // blocks fit an SM and one block's loads overlap the other's tensor-core work
+    static constexpr uint32_t FWD_H1 = X;
+    static constexpr uint32_t FWD_END = W2 + 8192;         // 106,496
 };
 
 constexpr int TMEM_D1 = 0, TMEM_D2 = 64, TMEM_D3 = 128, TMEM_E0 = 192, TMEM_E1 = 256, TMEM_E2 = 320;
@@ -252,7 +285,7 @@ __device__ __forceinline__ void mma_tile(uint32_t tmem_d, uint32_t a_base, int a
 }
 
 // ------------------------------------------------------------------ forward (inference)
-__global__ void __launch_bounds__(128, 1) k_mlp_forward(const float* __restrict__ prm, const float* __restrict__ X,
+__global__ void __launch_bounds__(128, 2) k_mlp_forward(const float* __restrict__ prm, const float* __restrict__ X,
                                                         int n, float* __restrict__ y, int* err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -281,7 +314,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward(const float* __restrict_
     for (int tile = blockIdx.x; tile * 128 < n && ok; tile += gridDim.x) {
         const int r0 = tile * 128;
         const int valid = min(128, n - r0);
-        stage_rows(sm + MlpSmem::X, X + (size_t)r0 * MLP_IN, 128, valid, MLP_IN, MLP_IN);
+        stage_rows_stream(sm + MlpSmem::X, X + (size_t)r0 * MLP_IN, 128, valid, MLP_IN, MLP_IN);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -302,13 +335,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward(const float* __restrict_
             for (int i = 0; i < 16; ++i) h[16 * c + i] = gelu(r[i] + b1s[16 * c + i]);
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) st_chunk(sm + MlpSmem::H1, t, 8 * c, 128, h + 8 * c);
+        for (int c = 0; c < 8; ++c) st_chunk(sm + MlpSmem::FWD_H1, t, 8 * c, 128, h + 8 * c);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         if (t == 0) {
             tc_fence_after();
-            mma_tile(tmem + TMEM_D2, sbase + MlpSmem::H1, 128, sbase + MlpSmem::W2, MLP_H, MLP_H, MLP_H, 0);
+            mma_tile(tmem + TMEM_D2, sbase + MlpSmem::FWD_H1, 128, sbase + MlpSmem::W2, MLP_H, MLP_H, MLP_H, 0);
             mma_commit(smem_addr(&mbar));
         }
         ok = ok && mbar_wait(smem_addr(&mbar), phase);
@@ -668,7 +701,13 @@ extern "C" int vrc_mlp_predict(const vrc_mlp* m, const float* d_feat, int32_t n,
     if (n == 0) return VRC_OK;
     if (!d_feat || !d_logr) return VRC_ERR_INVALID;
     if ((reinterpret_cast<uintptr_t>(d_feat) & 15) != 0) return VRC_ERR_INVALID;
-    k_mlp_forward<<<mlp_grid(n), 128, MlpSmem::FWD_END + 1024, (cudaStream_t)stream>>>(m->params, d_feat, n, d_logr,
+    int fwd_blocks = mlp_grid(n);
+    {
+        // two forward blocks fit an SM (106 KB of shared memory, 128 TMEM columns each)
+        int tiles = (n + 127) / 128, per2 = 2 * fwd_blocks;
+        fwd_blocks = tiles < per2 ? (tiles < 1 ? 1 : tiles) : per2;
+    }
+    k_mlp_forward<<<fwd_blocks, 128, MlpSmem::FWD_END + 1024, (cudaStream_t)stream>>>(m->params, d_feat, n, d_logr,
                                                                                       m->err);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }

@@ -29,6 +29,7 @@ class FrameResult:
     misses: int = 0
     placement: object = None
     placement2: object = None      # the multiple-scattering cache when split
+    placement_s: float = 0.0       # time in placement (records, grids, coverage), prepass and repairs
 
 
 def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int = 4, mlp=None, coarse_params=None,
@@ -42,6 +43,7 @@ def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int
     caches = [replace(params, parts=1), replace(params, parts=2)] if split else [params]
     pls = [place(scene, p, pts, start_level, max_level, mlp, coarse_params, cell_over_radius, valid=valid,
                  aniso=aniso) for p in caches]
+    placement_s = sum(pl.seconds for pl in pls)
     passes = [("prepass", int(pts.shape[0]), sum(pl.n_records for pl in pls))]
     img = torch.empty((W * H, 3), dtype=torch.float32, device="cuda")
     miss = torch.empty((W * H,), dtype=torch.int32, device="cuda")
@@ -63,8 +65,10 @@ def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int
         before = sum(pl.n_records for pl in pls)
         pls = [place(scene, p, mpts, max_level, max_level, None, None, cell_over_radius, valid=mvalid, base=pl,
                      capacity=pl.n_records + int(mpts.shape[0]), aniso=aniso) for p, pl in zip(caches, pls)]
+        placement_s += sum(pl.seconds for pl in pls)
         passes.append(("repair", m, sum(pl.n_records for pl in pls) - before))
         render_pixels(scene, pls[0].grid, cam, plist, steps, img, miss, grid2=grid2())
     torch.cuda.synchronize()
     return FrameResult(image=img, seconds=time.perf_counter() - t0, n_records=sum(pl.n_records for pl in pls),
-                       passes=passes, misses=misses, placement=pls[0], placement2=pls[1] if split else None)
+                       passes=passes, misses=misses, placement=pls[0], placement2=pls[1] if split else None,
+                       placement_s=placement_s)

@@ -244,3 +244,15 @@ def test_prepass_matches_in_kernel_tracing(vrc):
     a = run_gpu(vrc, w.scene, w.params, pos[:8], debug_hits=True)
     b = run_gpu(vrc, w.scene, w.params, pos[:8], debug_hits=True, tuning=dict(no_prepass=1))
     assert np.array_equal(a["hit_prim"], b["hit_prim"]) and np.array_equal(a["hit_t"], b["hit_t"])
+
+
+def test_prepass_in_batches_matches_in_kernel_tracing(vrc):
+    """33,000 records of 2,050 rays exceed the pre-pass buffers (64 Mi rays), so the launch
+    runs as two batches of work items; the records equal those the record kernel computes
+    when it traces its own primary rays."""
+    w = W.config2()
+    pos = w.positions(33000, seed=29)
+    a = run_gpu(vrc, w.scene, w.params, pos)
+    b = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(no_prepass=1))
+    for k in ("L", "grad", "hess", "radius", "status", "n_cells"):
+        assert np.array_equal(a[k], b[k]), k
