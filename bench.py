@@ -366,13 +366,16 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
         if not args.no_cpu_baseline:
             n_rec, n_q = w.n_records, min(w.n_queries, 131072)
             rr, qr, spent = oracle_rates(w, n_rec, n_q, os.cpu_count() or 1)
+            rr1, _, spent1 = oracle_rates(w, 32, 256, 1)          # one host thread, for the ratio
+            spent += spent1
             t_cpu = w.n_records / rr + w.n_queries / qr
             line["cpu_baseline"] = {"value": w.n_records / t_cpu, "unit": "records/s", "cores": os.cpu_count(),
                                     "kind": "oracle", "cpu": cpu_model(),
                                     "sample": f"all {n_rec} records (one per host thread at a time) and {n_q} of the "
                                               f"{w.n_queries} queries (brute force over all records, 1 thread); "
                                               "query time scaled to the full batch",
-                                    "records_per_s": rr, "queries_per_s": qr, "seconds": spent}
+                                    "records_per_s": rr, "records_per_s_1_thread": rr1, "queries_per_s": qr,
+                                    "seconds": spent}
         print(json.dumps(line), flush=True)
     return line
 
