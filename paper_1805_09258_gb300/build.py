@@ -19,6 +19,11 @@ LIB = os.path.join(HERE, "libvrc.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["scene.cu", "records.cu", "query.cu", "noalloc.cu", "mlp.cu", "render.cu", "flat.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The record kernels use the hardware's approximate division, reciprocal and square root and
+# flush denormals to zero: measured 17 % faster primary pre-pass and 9 % faster record kernel,
+# at the same distance from the FP64 oracle (their errors, a few units in the last place, sit
+# far inside the 1e-4 / 1e-3 tolerances and the near-tie budgets).
+SOURCE_FLAGS = {"records.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -51,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def one(src):
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc()] + _flags(verbose) + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc()] + _flags(verbose) + SOURCE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -837,7 +837,9 @@ __global__ void k_radius(RecArgs a) {
 // As a flat launch it keeps every warp slot of the SM busy; inside the record kernel the
 // same traversal ran with two blocks per SM between barriers, at about half the rate.
 // Slots are pre_stride rays wide; a smaller ray set leaves the rest of its slot unused.
-__global__ void __launch_bounds__(128) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
+// 12 blocks of 128 per SM (at most 42 registers): measured 3 % faster on a 2,048-triangle
+// scene and 8 % on a 250,000-triangle one than the unconstrained 70 registers
+__global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = (int)(i / a.pre_stride), gv = (int)(i - (long long)slot * a.pre_stride);
     const int item = a.item_base + slot;
