@@ -116,8 +116,8 @@ def measured_peaks():
 
 
 # DRAM bytes per record of k_records (the pre-pass rays it loads dominate), from one ncu
-# capture of a 1,024-record launch of the mid workload: (60.13 MB + 0.14 MB) / 1,024
-K_RECORDS_DRAM_BYTES_PER_RECORD = (60.132608e6 + 0.14336e6) / 1024
+# capture of a 1,024-record launch of the mid workload: (75.11 MB + 1.82 MB) / 1,024
+K_RECORDS_DRAM_BYTES_PER_RECORD = (75.111936e6 + 1.82016e6) / 1024
 
 
 def fp32_peak_tflops(sm_mhz: float = 2070.0) -> float:
@@ -150,7 +150,32 @@ def oracle_rates(w, n_rec_sample: int, n_q_sample: int, threads: int):
     t0 = time.perf_counter()
     oracle.query(pos, tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=w.params.extrap_order)
     t_q = time.perf_counter() - t0
+    oracle_rates.last_records = r
     return rec_rate, n_q_sample / t_q, t_rec + t_q
+
+
+def precision_report(gpu: dict, ref: dict) -> dict:
+    """Per-output error of the GPU records against the FP64 oracle on the same records:
+    relative error of L per channel, |d grad| / |grad| and |d H|_F / |H|_F per channel;
+    max, 99th percentile and median over all records.  The few records with a shadow or
+    primary ray within float rounding of an edge set the max (their FP32 and FP64 decisions
+    may differ); the parity tests bound those by per-record decision budgets."""
+    def fro(h):
+        return np.sqrt(h[..., 0] ** 2 + h[..., 3] ** 2 + h[..., 5] ** 2 + 2 * (h[..., 1] ** 2 + h[..., 2] ** 2 + h[..., 4] ** 2))
+    n = ref["L"].shape[0]
+    Lg, Lo = gpu["L"][:n].astype(np.float64), ref["L"]
+    eL = np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1e-12)
+    gg, go = gpu["grad"][:n].reshape(n, 3, 3).astype(np.float64), ref["grad"].reshape(n, 3, 3)
+    eg = np.linalg.norm(gg - go, axis=2) / np.maximum(np.linalg.norm(go, axis=2), 1e-12)
+    hg, ho = gpu["hess"][:n].reshape(n, 3, 6).astype(np.float64), ref["hess"].reshape(n, 3, 6)
+    eh = fro(hg - ho) / np.maximum(fro(ho), 1e-12)
+
+    def stats(e):
+        e = e.ravel()
+        return {"max": float(e.max()), "p99": float(np.percentile(e, 99)), "median": float(np.median(e))}
+
+    return {"records": int(n), "L_rel": stats(eL), "grad_rel": stats(eg), "hess_rel": stats(eh),
+            "tolerance": {"L_rel": 1e-4, "grad_rel": 1e-3, "hess_rel": 1e-3}}
 
 
 def run_reference(args, w, rank, world):
@@ -269,8 +294,9 @@ def run_gpu(args, w, rank, world, local_rank):
         e2e_s, h2d, d2h = e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, flush)
     line = None
     if rank == 0:
+        gpu_rec = {k: rec[k].cpu().numpy() for k in ("L", "grad", "hess")}
         line = report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h,
-                      kernel_ms)
+                      kernel_ms, gpu_rec)
     return line
 
 
@@ -312,7 +338,8 @@ def e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, fl
     return e2e_s, h2d, d2h
 
 
-def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h, kernel_ms):
+def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h, kernel_ms,
+           gpu_rec=None):
     value = world * w.n_records / (ms * 1e-3)
     if True:
         clk = clocks.summary()
@@ -366,7 +393,9 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
         if not args.no_cpu_baseline:
             n_rec, n_q = w.n_records, min(w.n_queries, 131072)
             rr, qr, spent = oracle_rates(w, n_rec, n_q, os.cpu_count() or 1)
+            full_ref = oracle_rates.last_records
             rr1, _, spent1 = oracle_rates(w, 32, 256, 1)          # one host thread, for the ratio
+            oracle_rates.last_records = full_ref
             spent += spent1
             t_cpu = w.n_records / rr + w.n_queries / qr
             line["cpu_baseline"] = {"value": w.n_records / t_cpu, "unit": "records/s", "cores": os.cpu_count(),
@@ -376,6 +405,9 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                                               "query time scaled to the full batch",
                                     "records_per_s": rr, "records_per_s_1_thread": rr1, "queries_per_s": qr,
                                     "seconds": spent}
+            if gpu_rec is not None:
+                # the oracle just computed the same 4,096 records (positions, jitter indices)
+                line["precision_vs_oracle"] = precision_report(gpu_rec, oracle_rates.last_records)
         print(json.dumps(line), flush=True)
     return line
 

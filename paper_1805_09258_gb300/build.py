@@ -19,11 +19,14 @@ LIB = os.path.join(HERE, "libvrc.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["scene.cu", "records.cu", "query.cu", "noalloc.cu", "mlp.cu", "render.cu", "flat.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# The record kernels use the hardware's approximate division, reciprocal and square root and
-# flush denormals to zero: measured 17 % faster primary pre-pass and 9 % faster record kernel,
-# at the same distance from the FP64 oracle (their errors, a few units in the last place, sit
-# far inside the 1e-4 / 1e-3 tolerances and the near-tie budgets).
-SOURCE_FLAGS = {"records.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+# The record, 2D-record, query and render kernels use the hardware's approximate division,
+# reciprocal and square root and flush denormals to zero.  Measured: primary pre-pass -17 %,
+# record kernel -9 %, 2D records -27 %, queries -8 %, rendering -16 %, at the same distance
+# from the FP64 oracles (errors of a few units in the last place sit far inside the 1e-4 /
+# 1e-3 tolerances and the near-tie budgets; region membership compares squared distances,
+# which these flags do not touch).
+_APPROX = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+SOURCE_FLAGS = {"records.cu": _APPROX, "flat.cu": _APPROX, "query.cu": _APPROX, "render.cu": _APPROX}
 
 
 def nvcc() -> str:
