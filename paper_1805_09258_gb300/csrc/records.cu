@@ -47,8 +47,6 @@ struct RecArgs {
     const float* pre_Lo;         // [item - item_base][pre_stride][3]
     int pre_stride;              // rays per pre-pass slot (the largest ray set of the launch)
     int item_base, item_end;     // work items of the current batch (positions in `order`)
-    int slot_by_rec;             // 1: pre-pass slot = record index (order set after the pre-pass)
-    int* tmax_bits;              // nullable: per-record max t_end (float bits) written by k_primary
 };
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -387,9 +385,6 @@ __device__ __noinline__ void write_ellipsoid(const double h[6], const double lam
 // Registers are capped at 128 per thread (2 blocks of 256 per SM): the traversal phases
 // are latency-bound and need the warps; a lower cap (85) spills the cell math and was
 // slower, an uncapped build took more registers and left one block per SM.
-#ifndef VRC_ORDER_BY_DEPTH
-#define VRC_ORDER_BY_DEPTH 1
-#endif
 #ifndef VRC_MERGE_LEFTOVERS
 #define VRC_MERGE_LEFTOVERS 1
 #endif
@@ -426,7 +421,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
         __syncthreads();
         const int rec = s_rec;
         if (rec >= a.n) break;
-        const int slot = a.slot_by_rec ? rec : s_item - a.item_base;   // pre-pass slot of this record
+        const int slot = s_item - a.item_base;           // pre-pass slot of this record
         const int nb = a.n_bands ? a.n_bands[rec] : a.nb0;
         if (a.n_bands && (nb < 2 || nb > a.nb0)) {
             // a per-record band count outside [2, params n_bands] would overrun the shared
@@ -870,19 +865,6 @@ __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, flo
     Lo_out[3 * i] = Lo.x;
     Lo_out[3 * i + 1] = Lo.y;
     Lo_out[3 * i + 2] = Lo.z;
-    if (a.tmax_bits) {
-        // the record's deepest ray sets its shell count; one atomic per warp when the
-        // warp's rays belong to one record (non-negative floats order as ints)
-        const unsigned act = __activemask();
-        const int bits = __float_as_int(te);
-        const int rec0 = __shfl_sync(act, rec, __ffs(act) - 1);
-        if (__all_sync(act, rec == rec0)) {
-            const int m = __reduce_max_sync(act, bits);
-            if ((threadIdx.x & 31) == __ffs(act) - 1) atomicMax(&a.tmax_bits[rec], m);
-        } else {
-            atomicMax(&a.tmax_bits[rec], bits);
-        }
-    }
     if (a.out.hit_prim) {
         size_t o = (size_t)rec * a.out.dbg_stride + gv;
         a.out.hit_prim[o] = prim;
@@ -903,6 +885,51 @@ static cudaEvent_t* timing_slot(vrc_scene* s, cudaStream_t st) {
         s->t_ev_made = s->n_timed + 1;
     }
     return s->t_ev[s->n_timed++];
+}
+
+// Records per pre-pass batch: the pre-pass buffers hold `cap` rays of `stride`-ray slots.
+static int batch_records(long long cap, int stride, int n) {
+    long long b = cap / stride;
+    return (int)(b < 1 ? 1 : (b > n ? n : b));
+}
+
+template <int NT>
+int launch_records(vrc_scene* s, const RecArgs& a0, size_t smem, cudaStream_t st) {
+    auto kfn = k_records<NT>;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return VRC_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, smem) != cudaSuccess || per_sm < 1)
+        return VRC_ERR_UNSUPPORTED;
+    if (s->tuning.blocks_per_sm > 0 && s->tuning.blocks_per_sm < per_sm) per_sm = s->tuning.blocks_per_sm;
+    DevScene dv = s->dev;
+    dv.use_lb = s->tuning.shadow_bvh ? 0 : 1;
+    RecArgs a = a0;
+    // batches of work items (in `order` when given) whose ray sets fit the pre-pass buffers
+    const int B = a.pre_ray ? batch_records(s->pre_cap, a.pre_stride, a.n) : a.n;
+    const int n_batches = (a.n + B - 1) / B;
+    cudaEvent_t* ev = n_batches == 1 ? timing_slot(s, st) : nullptr;
+    if (ev) cudaEventRecord(ev[0], st);
+    for (int b0 = 0; b0 < a.n; b0 += B) {
+        a.item_base = b0;
+        a.item_end = b0 + B < a.n ? b0 + B : a.n;
+        const int nb_items = a.item_end - a.item_base;
+        if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), st) != cudaSuccess) return VRC_ERR_CUDA;
+        if (a.pre_ray) {
+            const long long rays = (long long)nb_items * a.pre_stride;
+            k_primary<<<(unsigned)((rays + 127) / 128), 128, 0, st>>>(dv, a, const_cast<float4*>(a.pre_ray),
+                                                                       const_cast<float*>(a.pre_Lo));
+        }
+        if (ev) cudaEventRecord(ev[1], st);
+        int grid = per_sm * s->sm_count;
+        if (grid > nb_items) grid = nb_items;
+        if (grid < 1) grid = 1;
+        kfn<<<grid, NT, smem, st>>>(dv, a);
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    k_radius<<<(a.n + 127) / 128, 128, 0, st>>>(a);
+    if (ev) cudaEventRecord(ev[3], st);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
 // Largest-first order of records with uneven ray counts (longest-processing-time
@@ -927,76 +954,6 @@ __global__ void k_lpt_scatter(const int* n_bands, int n, int* hist, int* order) 
     if (i < n) order[atomicAdd(&hist[256 - min(256, max(1, n_bands[i]))], 1)] = i;
 }
 
-// Uniform ray sets: after the pre-pass, records ordered by shell count K = ceil(max t_end /
-// dt), most shells first (a record's cost grows with its shells), by the same counting sort.
-__global__ void k_depth_key(const int* tmax_bits, int n, float dt, int* key) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) key[i] = min(255, max(1, 1 + (int)ceilf(__int_as_float(tmax_bits[i]) / dt)));
-}
-
-// Records per pre-pass batch: the pre-pass buffers hold `cap` rays of `stride`-ray slots.
-static int batch_records(long long cap, int stride, int n) {
-    long long b = cap / stride;
-    return (int)(b < 1 ? 1 : (b > n ? n : b));
-}
-
-template <int NT>
-int launch_records(vrc_scene* s, const RecArgs& a0, size_t smem, cudaStream_t st) {
-    auto kfn = k_records<NT>;
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return VRC_ERR_UNSUPPORTED;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, smem) != cudaSuccess || per_sm < 1)
-        return VRC_ERR_UNSUPPORTED;
-    if (s->tuning.blocks_per_sm > 0 && s->tuning.blocks_per_sm < per_sm) per_sm = s->tuning.blocks_per_sm;
-    DevScene dv = s->dev;
-    dv.use_lb = s->tuning.shadow_bvh ? 0 : 1;
-    RecArgs a = a0;
-    // batches of work items (in `order` when given) whose ray sets fit the pre-pass buffers
-    const int B = a.pre_ray ? batch_records(s->pre_cap, a.pre_stride, a.n) : a.n;
-    const int n_batches = (a.n + B - 1) / B;
-    if (n_batches > 1) a.tmax_bits = nullptr;       // shell counts are known per batch only
-    cudaEvent_t* ev = n_batches == 1 ? timing_slot(s, st) : nullptr;
-    if (ev) cudaEventRecord(ev[0], st);
-    for (int b0 = 0; b0 < a.n; b0 += B) {
-        a.item_base = b0;
-        a.item_end = b0 + B < a.n ? b0 + B : a.n;
-        const int nb_items = a.item_end - a.item_base;
-        if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), st) != cudaSuccess) return VRC_ERR_CUDA;
-        if (a.pre_ray) {
-            const long long rays = (long long)nb_items * a.pre_stride;
-            if (a.tmax_bits && cudaMemsetAsync(a.tmax_bits, 0, sizeof(int) * a.n, st) != cudaSuccess)
-                return VRC_ERR_CUDA;
-            k_primary<<<(unsigned)((rays + 127) / 128), 128, 0, st>>>(dv, a, const_cast<float4*>(a.pre_ray),
-                                                                       const_cast<float*>(a.pre_Lo));
-            if (a.tmax_bits) {
-                // most shells first: order [n] | histogram [258] | max t_end [n] | key [n]
-                int* order = s->d_order;
-                int* hist = order + a.n;
-                int* key = a.tmax_bits + a.n;
-                const int nbk = (a.n + 255) / 256;
-                k_depth_key<<<nbk, 256, 0, st>>>(a.tmax_bits, a.n, a.dt, key);
-                if (cudaMemsetAsync(hist, 0, sizeof(int) * 258, st) != cudaSuccess) return VRC_ERR_CUDA;
-                k_lpt_hist<<<nbk, 256, 0, st>>>(key, a.n, hist);
-                k_lpt_scan<<<1, 32, 0, st>>>(hist);
-                k_lpt_scatter<<<nbk, 256, 0, st>>>(key, a.n, hist, order);
-                a.order = order;
-                a.slot_by_rec = 1;
-            }
-        }
-        if (ev) cudaEventRecord(ev[1], st);
-        int grid = per_sm * s->sm_count;
-        if (grid > nb_items) grid = nb_items;
-        if (grid < 1) grid = 1;
-        kfn<<<grid, NT, smem, st>>>(dv, a);
-    }
-    if (ev) cudaEventRecord(ev[2], st);
-    k_radius<<<(a.n + 127) / 128, 128, 0, st>>>(a);
-    if (ev) cudaEventRecord(ev[3], st);
-    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
-}
-
-
 }  // namespace
 
 static int ensure_order_scratch(vrc_scene* s, int n) {
@@ -1004,8 +961,7 @@ static int ensure_order_scratch(vrc_scene* s, int n) {
     cudaFree(s->d_order);
     s->d_order = nullptr;
     s->order_cap = 0;
-    // order [n], histogram [258], per-record max t_end [n], sort key [n]
-    if (cudaMalloc((void**)&s->d_order, sizeof(int) * (3 * (size_t)n + 258)) != cudaSuccess) return VRC_ERR_OOM;
+    if (cudaMalloc((void**)&s->d_order, sizeof(int) * ((size_t)n + 258)) != cudaSuccess) return VRC_ERR_OOM;
     s->order_cap = n;
     return VRC_OK;
 }
@@ -1120,8 +1076,6 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.pre_stride = nb * ns + 2;                       // the largest ray set of the launch
     a.item_base = 0;
     a.item_end = n;
-    a.slot_by_rec = 0;
-    a.tmax_bits = nullptr;
     if (!s->tuning.no_prepass) {
         long long rays = (long long)n * a.pre_stride;
         if (rays > PRE_MAX_RAYS) rays = PRE_MAX_RAYS / a.pre_stride * a.pre_stride;
@@ -1131,14 +1085,6 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
             a.pre_Lo = s->d_pre_Lo;
         }
     }
-#if VRC_ORDER_BY_DEPTH
-    if (!d_n_bands && a.pre_ray && n > 1 && (long long)n * a.pre_stride <= s->pre_cap) {
-        // uniform ray sets: ordered by shell count once the pre-pass has traced them
-        int rc = ensure_order_scratch(s, n);
-        if (rc != VRC_OK) return rc;
-        a.tmax_bits = s->d_order + n + 258;
-    }
-#endif
     if (d_n_bands && n > 1) {
         // largest ray sets first; the order and histogram live in scene-owned scratch
         int rc = ensure_order_scratch(s, n);
@@ -1204,7 +1150,7 @@ extern "C" int vrc_records_graph_create(vrc_scene* s, const float* d_pos, int32_
                                         const vrc_record_params* p, const vrc_records_view* out, vrc_graph** g) {
     if (!s || !p || !out || !g || n < 1) return VRC_ERR_INVALID;
     *g = nullptr;
-    {
+    if (d_n_bands) {
         int rc = ensure_order_scratch(s, n);     // no allocation may happen inside the capture
         if (rc != VRC_OK) return rc;
     }
