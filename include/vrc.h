@@ -239,6 +239,13 @@ void vrc_destroy_grid(vrc_grid* grid);
 int vrc_build_record_grid_aniso(const vrc_records_view* recs, int32_t n, int32_t extrap_order, vrc_grid** out,
                                 void* stream);
 
+/* Rebuild `grid` in place from n records (spheres, or ellipsoids with aniso = 1), as
+ * vrc_build_record_grid(_aniso) would build it, reusing the grid's device buffers where
+ * they are large enough (growing them otherwise).  Same requirements, errors and
+ * synchronisation; on an error the grid may only be destroyed or rebuilt. */
+int vrc_rebuild_record_grid(vrc_grid* grid, const vrc_records_view* recs, int32_t n, int32_t extrap_order,
+                            int32_t aniso, void* stream);
+
 /* Answer nq queries d_q [nq][3] by Eq. radianceTaylor: the weighted first-order (or,
  * with extrap_order 2, second-order) Taylor extrapolation from every record k with
  * |x' - x_k| < R_k, weight w = 3d^2 - 2d^3, d = 1 - |x' - x_k| / R_k.  Writes d_rgb

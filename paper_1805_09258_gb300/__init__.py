@@ -88,6 +88,7 @@ def load_library(path: Optional[str] = None):
     L.vrc2d_destroy_scene.restype = None
     L.vrc2d_compute_records.argtypes = [P, P, I32, P, P, P]
     L.vrc_build_record_grid_aniso.argtypes = [P, I32, I32, C.POINTER(C.c_void_p), P]
+    L.vrc_rebuild_record_grid.argtypes = [P, P, I32, I32, I32, P]
     L.vrc_destroy_grid.argtypes = [P]
     L.vrc_destroy_grid.restype = None
     L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
@@ -403,6 +404,18 @@ class Grid:
         self.n = n
         self.extrap_order = extrap_order
         self.aniso = aniso
+
+    def rebuild(self, records: dict, n: Optional[int] = None, stream=None):
+        """vrc_rebuild_record_grid: the same grid object rebuilt from new records, reusing
+        its device buffers."""
+        n = records["L"].shape[0] if n is None else n
+        v = records_view(records)
+        self._keep = records
+        rc = load_library().vrc_rebuild_record_grid(self.handle, C.byref(v), n, self.extrap_order, int(self.aniso),
+                                                    _stream_ptr(stream))
+        _check(rc, "vrc_rebuild_record_grid")
+        self.n = n
+        return self
 
     def __del__(self):
         try:

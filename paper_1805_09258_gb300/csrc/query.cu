@@ -298,16 +298,27 @@ extern "C" void vrc_destroy_grid(vrc_grid* g) {
 
 namespace {
 
-int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, vrc_grid** out, void* stream) {
-    if (!v || !out || n < 0 || (order != 1 && order != 2)) return VRC_ERR_INVALID;
+// grow a buffer of `cap` elements to at least `need` (its contents are not kept)
+template <typename T>
+int grow(T** p, long long* cap, long long need) {
+    if (need < 1) need = 1;
+    if (*cap >= need) return VRC_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void**)p, sizeof(T) * (size_t)need) != cudaSuccess) {
+        *p = nullptr;
+        return VRC_ERR_OOM;
+    }
+    *cap = need;
+    return VRC_OK;
+}
+
+// (re)build grid g from n records, reusing its buffers where they are large enough
+int fill_grid(vrc_grid* g, const vrc_records_view* v, int32_t n, int32_t order, bool aniso, cudaStream_t st) {
+    if (!v || n < 0 || (order != 1 && order != 2)) return VRC_ERR_INVALID;
     if (n > 0 && (!v->pos || !v->L || !v->grad || (order == 2 && !v->hess))) return VRC_ERR_INVALID;
     if (n > 0 && (aniso ? (!v->radii || !v->axes) : !v->radius)) return VRC_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
-    *out = nullptr;
-    vrc_grid* g = new vrc_grid();
-    g->n = n;
-    g->order = order;
-    g->aniso = aniso ? 1 : 0;
     // cell size: about a quarter of the median radius (ellipsoids: of the geometric mean
     // of the principal radii), at most 64 cells per axis
     int G = 1;
@@ -315,10 +326,8 @@ int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, 
         std::vector<float> R(aniso ? 3 * (size_t)n : (size_t)n);
         if (cudaMemcpyAsync(R.data(), aniso ? v->radii : v->radius, sizeof(float) * R.size(), cudaMemcpyDeviceToHost,
                             st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            vrc_destroy_grid(g);
+            cudaStreamSynchronize(st) != cudaSuccess)
             return VRC_ERR_CUDA;
-        }
         if (aniso) {
             for (int k = 0; k < n; ++k) R[k] = std::cbrt(R[3 * k] * R[3 * k + 1] * R[3 * k + 2]);
             R.resize(n);
@@ -329,49 +338,70 @@ int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, 
         G = (int)std::ceil(4.0f / med);
         G = std::max(1, std::min(64, G));
     }
-    g->G = G;
-    int ncell = G * G * G;
-    int nblk = (ncell + 1 + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    const int ncell = G * G * G;
+    const int nblk = (ncell + 1 + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    long long ext_cap = g->ell_cap / 2;   // ext holds one float4 per record, ell two
     int rc = VRC_OK;
-    if ((rc = dev_alloc(&g->rec, 4 * (size_t)n)) || (rc = dev_alloc(&g->hess, order == 2 ? 5 * (size_t)n : 1)) ||
-        (aniso && ((rc = dev_alloc(&g->ell, 2 * (size_t)n)) || (rc = dev_alloc(&g->ext, (size_t)n)))) ||
-        (rc = dev_alloc(&g->cell_start, (size_t)ncell + 1)) || (rc = dev_alloc(&g->q_count, (size_t)ncell + 1)) ||
-        (rc = dev_alloc(&g->scan_tmp, (size_t)nblk + 1))) {
-        vrc_destroy_grid(g);
+    if ((rc = grow(&g->rec, &g->rec_cap, 4 * (long long)n)) ||
+        (order == 2 && (rc = grow(&g->hess, &g->hess_cap, 5 * (long long)n))) ||
+        (rc = grow(&g->cell_start, &g->cell_cap, (long long)ncell + 1)) ||
+        (rc = grow(&g->scan_tmp, &g->scan_cap, (long long)nblk + 1)))
         return rc;
+    if (aniso) {
+        if (g->ell_cap < 2 * (long long)n) {
+            cudaFree(g->ext);
+            g->ext = nullptr;
+            ext_cap = 0;
+            if ((rc = grow(&g->ell, &g->ell_cap, 2 * (long long)n)) || (rc = grow(&g->ext, &ext_cap, (long long)n)))
+                return rc;
+        }
     }
+    // query scratch: cell counts sized like cell_start
+    if (g->q_count == nullptr || g->cell_cap > g->q_count_cap) {
+        cudaFree(g->q_count);
+        g->q_count = nullptr;
+        g->q_count_cap = 0;
+        if (cudaMalloc((void**)&g->q_count, sizeof(int) * (size_t)g->cell_cap) != cudaSuccess) return VRC_ERR_OOM;
+        g->q_count_cap = g->cell_cap;
+    }
+    g->n = n;
+    g->order = order;
+    g->aniso = aniso ? 1 : 0;
+    g->G = G;
     if (n > 0) {
         int tb = 256, nbk = (n + tb - 1) / tb;
         k_pack<<<nbk, tb, 0, st>>>(*v, n, order, g->rec, g->hess);
         if (aniso) k_pack_ellipsoid<<<nbk, tb, 0, st>>>(*v, n, g->rec, g->ell, g->ext);
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
         int nwb = (int)(((long long)n * 32 + tb - 1) / tb);   // one warp per record
-        k_insert<false><<<nwb, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, nullptr, nullptr);
+        k_insert<false><<<nwb, tb, 0, st>>>(g->rec, aniso ? g->ext : nullptr, n, G, g->q_count, nullptr, nullptr);
         exclusive_scan(g->q_count, ncell, g->cell_start, g->scan_tmp, st);
         int total = 0;
         if (cudaMemcpyAsync(&total, g->cell_start + ncell, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            vrc_destroy_grid(g);
+            cudaStreamSynchronize(st) != cudaSuccess)
             return VRC_ERR_CUDA;
-        }
         g->entries = total;
-        if ((rc = dev_alloc(&g->cell_list, (size_t)total))) {
-            vrc_destroy_grid(g);
-            return rc;
-        }
+        if ((rc = grow(&g->cell_list, &g->list_cap, (long long)total))) return rc;
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
-        k_insert<true><<<nwb, tb, 0, st>>>(g->rec, g->ext, n, G, g->q_count, g->cell_start, g->cell_list);
+        k_insert<true><<<nwb, tb, 0, st>>>(g->rec, aniso ? g->ext : nullptr, n, G, g->q_count, g->cell_start,
+                                           g->cell_list);
         k_sort_lists<<<ncell, 256, 0, st>>>(g->cell_start, ncell, g->cell_list);
     } else {
+        g->entries = 0;
         cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);
-        if ((rc = dev_alloc(&g->cell_list, 1))) {
-            vrc_destroy_grid(g);
-            return rc;
-        }
+        if ((rc = grow(&g->cell_list, &g->list_cap, 1))) return rc;
     }
-    if (cudaGetLastError() != cudaSuccess) {
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+int build_grid(const vrc_records_view* v, int32_t n, int32_t order, bool aniso, vrc_grid** out, void* stream) {
+    if (!out) return VRC_ERR_INVALID;
+    *out = nullptr;
+    vrc_grid* g = new vrc_grid();
+    int rc = fill_grid(g, v, n, order, aniso, (cudaStream_t)stream);
+    if (rc != VRC_OK) {
         vrc_destroy_grid(g);
-        return VRC_ERR_CUDA;
+        return rc;
     }
     *out = g;
     return VRC_OK;
@@ -387,6 +417,12 @@ extern "C" int vrc_build_record_grid(const vrc_records_view* v, int32_t n, int32
 extern "C" int vrc_build_record_grid_aniso(const vrc_records_view* v, int32_t n, int32_t order, vrc_grid** out,
                                            void* stream) {
     return build_grid(v, n, order, true, out, stream);
+}
+
+extern "C" int vrc_rebuild_record_grid(vrc_grid* g, const vrc_records_view* v, int32_t n, int32_t order, int32_t aniso,
+                                       void* stream) {
+    if (!g || aniso < 0 || aniso > 1) return VRC_ERR_INVALID;
+    return fill_grid(g, v, n, order, aniso != 0, (cudaStream_t)stream);
 }
 
 extern "C" int vrc_query_inscatter(const vrc_grid* gc, const float* d_q, int32_t nq, float* d_rgb,

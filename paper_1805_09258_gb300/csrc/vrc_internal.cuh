@@ -91,6 +91,8 @@ struct vrc_grid {
     int* q_count;          // [G^3 + 1]
     int* scan_tmp;         // block sums
     int q_cap;
+    // capacities of the buffers above (elements), kept across vrc_rebuild_record_grid
+    long long rec_cap, hess_cap, ell_cap, cell_cap, scan_cap, list_cap, q_count_cap;
 };
 
 // ------------------------------------------------------------------ small vector ops

@@ -78,6 +78,7 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
     total = prev
     res = PlacementResult(0)
     grid = base.grid if base is not None else None
+    base_grid = grid                      # the caller's grid is never rebuilt in place
     if grid is not None:
         query_inscatter(grid, cand, rgb, count)
         update_coverage(count, level)
@@ -90,7 +91,10 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         compute_records(scene, pts[:m].contiguous(), params, out=out)
         total += m
         view = {k: v[:total] for k, v in recs.items()}
-        grid = Grid(view, n=total, aniso=aniso)
+        if grid is not None and grid is not base_grid and grid.aniso == aniso:
+            grid.rebuild(view, n=total)
+        else:
+            grid = Grid(view, n=total, aniso=aniso)
         query_inscatter(grid, cand, rgb, count)
         update_coverage(count, level)
 

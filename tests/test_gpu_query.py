@@ -113,3 +113,30 @@ def test_records_then_queries_end_to_end(vrc):
     assert np.array_equal(cnt[~sensitive], qc[~sensitive])
     both = (~sensitive) & (qc > 0)
     assert np.all(np.abs(rgb[both] - qo[both]) <= 2e-3 * np.abs(qo[both]).max(axis=1, keepdims=True) + 1e-6)
+
+
+def test_rebuild_in_place_matches_a_new_grid(vrc):
+    """vrc_rebuild_record_grid: one grid object rebuilt from tables of other sizes, radii and
+    kinds (spheres, then ellipsoids, then spheres) answers exactly as a newly built grid."""
+    rng = np.random.default_rng(61)
+    q = torch.from_numpy(rng.uniform(0, 1, size=(30000, 3)).astype(np.float32)).cuda()
+    grid = None
+    for n, seed, r_hi, aniso in ((500, 62, 0.3, False), (3000, 63, 0.1, False), (50, 64, 0.45, True),
+                                 (2000, 65, 0.2, False), (0, 66, 0.2, False)):
+        tab = synthetic_table(max(n, 1), seed, r_hi=r_hi)
+        tab = {k: v[:n] for k, v in tab.items()}
+        if aniso:
+            tab["radii"] = np.repeat(tab["radius"][:, None], 3, axis=1).astype(np.float32) * \
+                np.array([1.0, 0.5, 0.8], np.float32)
+            tab["axes"] = np.tile(np.eye(3, dtype=np.float32).ravel(), (n, 1))
+        recs = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in tab.items()}
+        fresh = vrc.Grid(recs, n=n, aniso=aniso)
+        a_rgb, a_cnt = vrc.query_inscatter(fresh, q)
+        if grid is None:
+            grid = vrc.Grid(recs, n=n, aniso=aniso)
+        else:
+            grid.aniso = aniso
+            grid.rebuild(recs, n=n)
+        b_rgb, b_cnt = vrc.query_inscatter(grid, q)
+        torch.cuda.synchronize()
+        assert torch.equal(a_cnt, b_cnt) and torch.equal(a_rgb, b_rgb), (n, aniso)
