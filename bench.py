@@ -579,6 +579,97 @@ def run_mlp(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Extra measurement (not the default line): learned vs plain placement on the learned
+    workload (mid-style scenes).  The predictor is trained on records of 8 scenes (seeds
+    1..8); on a held-out scene (seed 41) 60,000 candidate points are covered by plain and by
+    learned placement at three tolerances; the error is the cache's per-point relative
+    luminance error at 619 held-out candidates against a 64x128-ray record there (mean,
+    median, 90th percentile; the RMSE over the mean, which a few bright points near the light
+    dominate, is reported too, and so is the reference's own noise), and the learned path's
+    placement time is compared with the plain path's at equal mean error (log-log
+    interpolation between the two nearest plain tolerances)."""
+    import torch
+    import oracle.mlp as M
+    import paper_1805_09258_gb300 as vrc
+    from paper_1805_09258_gb300 import build as vbuild, learned, placement
+    vbuild.build()
+    coarse = W.RecordParams(n_bands=8, n_bins=16, seed=W.configs.SEED_JITTER + 1000)
+    t0 = time.perf_counter()
+    ex = learned.ExampleSet(8 * 8192)
+    for seed in range(1, 9):
+        w = W.config4(scene_seed=seed)
+        ex.add(vrc.Scene.from_workload(w.scene), w.positions(8192, seed=100 + seed), w.params, coarse)
+    F, T = ex.view(shuffle=True)
+    mlp = vrc.MLP(M.init_params(21))
+    learned.train(mlp, F, T, steps=1500, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    w = W.config4(scene_seed=41)
+    s = vrc.Scene.from_workload(w.scene)
+    cand = torch.from_numpy(w.positions(60000, seed=441)).cuda()
+    q = cand[torch.arange(0, cand.shape[0], 97, device="cuda")].contiguous()
+    rp_ref = W.configs.replace(w.params, n_bands=64, n_bins=128, seed=W.configs.SEED_JITTER + 7)
+    ref = vrc.compute_records(s, q, rp_ref, full=False)["L"].cpu().numpy().astype(np.float64)
+    ref2 = vrc.compute_records(s, q, W.configs.replace(rp_ref, seed=W.configs.SEED_JITTER + 8),
+                               full=False)["L"].cpu().numpy().astype(np.float64)
+
+    Y = np.array([0.2126, 0.7152, 0.0722])
+    Yref = ref @ Y
+    floor = 1e-2 * np.mean(np.abs(Yref))
+
+    def rel_err(L):
+        """Per-point relative luminance error (denominator floored at 1 % of the mean)."""
+        return np.abs(L @ Y - Yref) / np.maximum(np.abs(Yref), floor)
+
+    def rel_rmse(L):
+        return float(np.sqrt(np.mean((L - ref) ** 2)) / np.mean(np.abs(ref)))
+
+    res = {}
+    for eps in (w.params.eps * 2, w.params.eps, w.params.eps / 2):
+        rp = W.configs.replace(w.params, eps=eps)
+        for name, kw in (("plain", {}), ("learned", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5))):
+            placement.place(s, rp, cand, **kw)                     # warm-up
+            torch.cuda.synchronize()
+            r = placement.place(s, rp, cand, **kw)
+            rgb, cnt = vrc.query_inscatter(r.grid, q)
+            L = rgb.cpu().numpy().astype(np.float64)
+            e = rel_err(L)
+            res[f"{name}_eps{eps:g}"] = {"records": r.n_records, "placement_ms": r.seconds * 1e3,
+                                         "mean_rel_err": float(e.mean()), "median_rel_err": float(np.median(e)),
+                                         "p90_rel_err": float(np.quantile(e, 0.9)), "rel_rmse": rel_rmse(L),
+                                         "uncovered": int((cnt == 0).sum())}
+    plain = sorted((v["mean_rel_err"], v["placement_ms"], v["records"]) for k, v in res.items()
+                   if k.startswith("plain"))
+    equal = {}
+    for k, v in res.items():
+        if not k.startswith("learned"):
+            continue
+        e = v["mean_rel_err"]
+        lo = [p for p in plain if p[0] <= e]
+        hi = [p for p in plain if p[0] >= e]
+        if lo and hi:
+            a, b = lo[-1], hi[0]
+            f_ = 0.0 if a[0] == b[0] else (math.log(e) - math.log(a[0])) / (math.log(b[0]) - math.log(a[0]))
+            t_ = math.exp(math.log(a[1]) + f_ * (math.log(b[1]) - math.log(a[1])))
+            n_ = math.exp(math.log(a[2]) + f_ * (math.log(b[2]) - math.log(a[2])))
+            equal[k] = {"mean_rel_err": e, "plain_ms_at_equal_error": t_, "learned_ms": v["placement_ms"],
+                        "speedup": t_ / v["placement_ms"], "plain_records_at_equal_error": n_,
+                        "learned_records": v["records"]}
+        else:
+            equal[k] = {"mean_rel_err": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
+    base = res[f"learned_eps{w.params.eps:g}"]
+    line = {"metric": METRIC, "value": cand.shape[0] / (base["placement_ms"] * 1e-3),
+            "unit": "candidate points covered/s (learned placement)", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "dtype": "f32 records, bf16 predictor", "data": "synthetic",
+            "config": {"workload": "learned: mid-style scene (seed 41), 60,000 candidates, records 32x64, "
+                                   "coarse features 8x16"},
+            "runs": res, "equal_error": equal, "mlp_training_s": train_s,
+            "reference_noise_floor": {"mean_rel_err": float(rel_err(ref2).mean()),
+                                      "rel_rmse": float(np.sqrt(np.mean((ref2 - ref) ** 2)) / np.mean(np.abs(ref)))}}
+    print(json.dumps(line), flush=True)
+
+
 def run_render(args, w):
     """Extra measurement (not the default line): one 1920x1080 frame of the render-shaped
     workload, plain vs learned placement (and ellipsoidal / split-cache variants), each at
@@ -689,7 +780,7 @@ def run_render(args, w):
                         "speedup": t / v["frame_ms"], "plain_records_at_equal_error": n,
                         "learned_records": v["records"]}
         else:
-            equal[k] = {"rel_rmse": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
+            equal[k] = {"mean_rel_err": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
     n_q = Wd * Hd * steps
     base = res[f"learned_eps{rp.eps:g}"]
     line = {"metric": METRIC, "value": n_q / (base["frame_ms"] * 1e-3), "unit": "march points/s (whole frame)",
@@ -717,8 +808,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat", "mlp"],
-                    help="mid (the default line), or the batching, render, 2D or MLP workload (extra measurements)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat", "mlp", "learned"],
+                    help="mid (the default line), or the batching, render, 2D, MLP or learned-placement workload "
+                         "(extra measurements)")
     args = ap.parse_args()
     if args.workload == "batching":
         run_batching(args, W.config3())
@@ -728,6 +820,9 @@ def main():
         return
     if args.workload == "mlp":
         run_mlp(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
     if args.workload == "flat":
         from workloads import flat
