@@ -457,6 +457,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
         }
         const int ns = a.n_bands ? 2 * nb : a.ns0;
         const int N = nb * ns;
+        // floor(n / ns) = umulhi(n, ns_m) for every n, ns below 2^16 (vertex and cell indices
+        // of a chunk stay below its shared-memory capacity)
+        const unsigned ns_m = 0xFFFFFFFFu / (unsigned)ns + 1u;
         const long long rid = a.rec_base + rec;
         const float3 x = f3(a.pos[3 * rec], a.pos[3 * rec + 1], a.pos[3 * rec + 2]);
         const float wmc = 4.0f * VRC_PI_F / (float)N;
@@ -482,14 +485,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 const int lv = vb + lane;
                 bool lit_v = false;
                 if (lv < nvert) {
-                int gv, row = 0;
-                bool pole = lv >= rows * ns;
-                if (!pole) {
-                    row = r0 + lv / ns;
-                    gv = row * ns + (lv - (lv / ns) * ns);
-                } else {
-                    gv = lv == PN ? N : N + 1;
-                }
+                const bool pole = lv >= rows * ns;
+                const int gv = !pole ? r0 * ns + lv : (lv == PN ? N : N + 1);
                 float3 d, Lo = f3(0.f, 0.f, 0.f);
                 float te;
                 int prim = -1;
@@ -519,7 +516,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 Lb[lv] = Lo.z;
                 lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
                 tmax_loc = fmaxf(tmax_loc, te);
-                bool owned = !pole && row < r1;
+                const bool owned = lv < (r1 - r0) * ns;        // a vertex of the rows this chunk owns
                 if (owned && prim >= 0) {
                     float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * te);
                     neumaier(mc[0], mcc[0], w * Lo.x);
@@ -565,9 +562,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         float3 Lo = f3(0.f, 0.f, 0.f);
                         if (tn < rv.w) {
                             Lo = medium_radiance(sc, x + d * tn, d);
-                            bool pole = lv >= rows * ns;
-                            bool owned = !pole && (r0 + lv / ns) < r1;
-                            if (owned) {
+                            if (lv < (r1 - r0) * ns) {                // a vertex of an owned row
                                 float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * tn);
                                 neumaier(mc[3], mcc[3], w * Lo.x);
                                 neumaier(mc[4], mcc[4], w * Lo.y);
@@ -587,12 +582,13 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 // per-warp queue so cell_eval runs with all 32 lanes busy
                 auto cell_verts = [&](int cc, int (&vi)[3]) {
                     if (north && cc < ns) {
-                        vi[0] = PN; vi[1] = cc; vi[2] = (cc + 1) % ns;
+                        vi[0] = PN; vi[1] = cc; vi[2] = cc + 1 == ns ? 0 : cc + 1;
                         return;
                     }
                     if (north) cc -= ns;
                     if (cc < 2 * ns * nq) {
-                        int qd = cc >> 1, ri = qd / ns, j = qd - ri * ns, j1 = (j + 1) % ns;
+                        int qd = cc >> 1, ri = (int)__umulhi((unsigned)qd, ns_m), j = qd - ri * ns;
+                        int j1 = j + 1 == ns ? 0 : j + 1;
                         int v00 = ri * ns + j, v01 = ri * ns + j1, v10 = (ri + 1) * ns + j, v11 = (ri + 1) * ns + j1;
                         if ((cc & 1) == 0) { vi[0] = v00; vi[1] = v10; vi[2] = v11; }
                         else { vi[0] = v00; vi[1] = v11; vi[2] = v01; }
@@ -600,7 +596,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     }
                     cc -= 2 * ns * nq;
                     int rl = (nb - 1 - r0) * ns;
-                    vi[0] = PS; vi[1] = rl + (cc + 1) % ns; vi[2] = rl + cc;
+                    vi[0] = PS; vi[1] = rl + (cc + 1 == ns ? 0 : cc + 1); vi[2] = rl + cc;
                 };
                 auto process = [&](int c) {
                     float v[32];
@@ -647,8 +643,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
 #pragma unroll
                         for (int q = 0; q < 3; ++q) any |= ((lmk[vi[q] >> 5] >> (vi[q] & 31)) & 1u) != 0u;
                     }
-                    if (any) {
-                        // a cell contributes iff one of its furthest vertices has radiance
+                    if (k == 0 && any) {
+                        // a cell contributes iff one of its furthest vertices has radiance.  On
+                        // a medium shell a vertex has radiance only while its ray is still open
+                        // (t_k < t_end), and then it sits at t_k, the furthest any vertex of the
+                        // cell can be: there a set bit alone decides
                         float tq[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
@@ -660,6 +659,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         for (int q = 0; q < 3; ++q)
                             if (tq[q] == tmx && (Lrk[vi[q]] != 0.f || Lgk[vi[q]] != 0.f || Lbk[vi[q]] != 0.f))
                                 lit = true;
+                    } else {
+                        lit = any;
                     }
                     unsigned msk = __ballot_sync(0xffffffffu, lit);
                     if (lit) wqw[qn + __popc(msk & ((1u << lane) - 1u))] = c;
@@ -841,8 +842,9 @@ __global__ void k_radius(RecArgs a) {
 // 12 blocks of 128 per SM (at most 42 registers): measured 3 % faster on a 2,048-triangle
 // scene and 8 % on a 250,000-triangle one than the unconstrained 70 registers
 __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = (int)(i / a.pre_stride), gv = (int)(i - (long long)slot * a.pre_stride);
+    // a batch holds at most PRE_MAX_RAYS (< 2^31) rays: 32-bit index arithmetic
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = (int)(i / (unsigned)a.pre_stride), gv = (int)(i - (unsigned)slot * (unsigned)a.pre_stride);
     const int item = a.item_base + slot;
     if (item >= a.item_end) return;
     const int rec = a.order ? a.order[item] : item;
