@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
     float* tot = mcs + NW * 12;                              // [128]
     int* misc = reinterpret_cast<int*>(tot + 128);           // [4]
     int* wq = misc + 4;                                      // [NW][64] lit-cell queues
-    const int LW = (a.cap + 31) >> 5;
+    const int LW = ((a.cap + 31) >> 5) + 1;                  // + 1: 32-bit windows may read one word past
     unsigned* litm = reinterpret_cast<unsigned*>(wq + NW * 64);   // [2][LW]: vertex has radiance (bit per vertex)
     int* wcnt = reinterpret_cast<int*>(litm + 2 * LW);            // [NW] leftover lit cells per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -631,37 +631,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 };
                 int* wqw = wq + warp * 64;
                 int qn = 0;
-                const int nround = (a.parts == 2 && k == 0) ? 0 : (ncell + 31) & ~31;   // MS cache: no surface shell
-                for (int base = warp * 32; base < nround; base += NT) {
-                    int c = base + lane;
-                    bool lit = false;
-                    int vi[3];
-                    bool any = false;
-                    if (c < ncell) {
-                        cell_verts(c, vi);
-                        const unsigned* lmk = litm + (k & 1) * LW;
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) any |= ((lmk[vi[q] >> 5] >> (vi[q] & 31)) & 1u) != 0u;
-                    }
-                    if (k == 0 && any) {
-                        // a cell contributes iff one of its furthest vertices has radiance.  On
-                        // a medium shell a vertex has radiance only while its ray is still open
-                        // (t_k < t_end), and then it sits at t_k, the furthest any vertex of the
-                        // cell can be: there a set bit alone decides
-                        float tq[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            float te = ray[vi[q]].w;
-                            tq[q] = (k == 0 || !(tk < te)) ? te : tk;
-                        }
-                        float tmx = fmaxf(tq[0], fmaxf(tq[1], tq[2]));
-#pragma unroll
-                        for (int q = 0; q < 3; ++q)
-                            if (tq[q] == tmx && (Lrk[vi[q]] != 0.f || Lgk[vi[q]] != 0.f || Lbk[vi[q]] != 0.f))
-                                lit = true;
-                    } else {
-                        lit = any;
-                    }
+                const unsigned* lmk = litm + (k & 1) * LW;
+                // appends the lanes' lit cells to the warp's queue; a full queue runs cell_eval
+                auto push = [&](int c, bool lit) {
                     unsigned msk = __ballot_sync(0xffffffffu, lit);
                     if (lit) wqw[qn + __popc(msk & ((1u << lane) - 1u))] = c;
                     qn += __popc(msk);
@@ -673,6 +645,151 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         __syncwarp();
                         qn -= 32;
                     }
+                };
+                // One loop, one push site (cell_eval is inlined once).  Surface shell: a cell
+                // contributes iff one of its furthest vertices (the largest ray parameter, ties
+                // included) has radiance; each lane tests one cell per step.  Medium shell: a
+                // vertex has radiance only while its ray is still open (t_k < t_end), and then
+                // it sits at t_k, the furthest any vertex of a cell can be, so a cell
+                // contributes iff one of its vertex bits is set.  Those cells are found 32 at a
+                // time by word operations on the bit rows: a segment is 32 bins of one quad row
+                // (its even and odd cells) or of a pole fan, segment s goes to lane s / NW of
+                // warp s % NW, and each step hands the warp's next 32 lit cells to its lanes.
+                const int SEG = (ns + 31) >> 5;
+                const int nseg = k == 0 ? 0 : (north ? SEG : 0) + nq * SEG + (south ? SEG : 0);
+                const int nround = (k != 0 || a.parts == 2) ? 0 : (ncell + 31) & ~31;   // MS cache: no surface shell
+                // bits [pos, pos + 32) of the vertex mask
+                auto win = [&](int pos) -> unsigned {
+                    const int w = pos >> 5;
+                    return __funnelshift_r(lmk[w], lmk[w + 1], pos & 31);
+                };
+                int base = warp * 32;                    // surface shell: next cell batch
+                int sb = 0, rb0 = 0, T = 0, excl = 0;    // medium shells: segment pass, step, lit count
+                unsigned me = 0u, mo = 0u;               // this lane's lit even / odd cells (fans: me)
+                int cb0 = 0, cstep = 1;                  // cell of bit p: cb0 + cstep p (+ 1 if odd)
+                for (;;) {
+                    int c = -1;
+                    bool lit = false;
+                    if (k == 0) {
+                        if (base >= nround) break;
+                        c = base + lane;
+                        base += NT;
+                        int vi[3];
+                        bool any = false;
+                        if (c < ncell) {
+                            cell_verts(c, vi);
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) any |= ((lmk[vi[q] >> 5] >> (vi[q] & 31)) & 1u) != 0u;
+                        }
+                        if (any) {
+                            float tq[3];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) tq[q] = ray[vi[q]].w;
+                            float tmx = fmaxf(tq[0], fmaxf(tq[1], tq[2]));
+#pragma unroll
+                            for (int q = 0; q < 3; ++q)
+                                if (tq[q] == tmx && (Lrk[vi[q]] != 0.f || Lgk[vi[q]] != 0.f || Lbk[vi[q]] != 0.f))
+                                    lit = true;
+                        }
+                    } else {
+                        if (rb0 >= T) {
+                            // next segment pass: this lane's segment, its lit masks, the prefix
+                            if (sb >= nseg) break;
+                            const int sg = sb + lane * NW + warp;
+                            sb += NT;
+                            me = 0u;
+                            mo = 0u;
+                            cb0 = 0;
+                            cstep = 1;
+                            if (sg < nseg) {
+                                int t = sg, kind, ri = 0, jb;
+                                if (north && t < SEG) {
+                                    kind = 0;
+                                    jb = t;
+                                } else {
+                                    if (north) t -= SEG;
+                                    if (t < nq * SEG) {
+                                        kind = 1;
+                                        ri = t / SEG;
+                                        jb = t - ri * SEG;
+                                    } else {
+                                        kind = 2;
+                                        jb = t - nq * SEG;
+                                    }
+                                }
+                                const int j0 = jb << 5, nv = min(32, ns - j0);
+                                const unsigned valid = nv == 32 ? 0xffffffffu : (1u << nv) - 1u;
+                                const unsigned wb = (j0 + nv == ns) ? 1u << (nv - 1) : 0u;   // bin ns - 1: next is bin 0
+                                // bins j and j + 1 (cyclic) of local vertex row rb
+                                auto row = [&](int rb, unsigned& R, unsigned& Rn) {
+                                    R = win(rb + j0);
+                                    Rn = win(rb + j0 + 1);
+                                    if (wb) Rn = ((lmk[rb >> 5] >> (rb & 31)) & 1u) ? (Rn | wb) : (Rn & ~wb);
+                                };
+                                if (kind == 1) {
+                                    unsigned R0, R0n, R1, R1n;
+                                    row(ri * ns, R0, R0n);
+                                    row((ri + 1) * ns, R1, R1n);
+                                    me = (R0 | R1 | R1n) & valid;        // (v00, v10, v11)
+                                    mo = (R0 | R1n | R0n) & valid;       // (v00, v11, v01)
+                                    cb0 = (north ? ns : 0) + 2 * (ri * ns + j0);
+                                    cstep = 2;
+                                } else {
+                                    const int pole = kind == 0 ? PN : PS;
+                                    unsigned R, Rn;
+                                    row(kind == 0 ? 0 : (nb - 1 - r0) * ns, R, Rn);
+                                    me = (((lmk[pole >> 5] >> (pole & 31)) & 1u) ? 0xffffffffu : (R | Rn)) & valid;
+                                    cb0 = kind == 0 ? j0 : (north ? ns : 0) + 2 * ns * nq + j0;
+                                }
+                            }
+                            const int cnt = __popc(me) + __popc(mo);
+                            int incl = cnt;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += y;
+                            }
+                            excl = incl - cnt;
+                            T = __shfl_sync(0xffffffffu, incl, 31);
+                            rb0 = 0;
+                            if (T == 0) continue;
+                        }
+                        // lane t of this step takes the warp's (rb0 + t)-th lit cell: its
+                        // source lane by a binary search over the exclusive prefix, then the
+                        // rank's bit in that lane's even mask, else in its odd mask
+                        const int t = rb0 + lane;
+                        rb0 += 32;
+                        int src = 0;
+#pragma unroll
+                        for (int st = 16; st >= 1; st >>= 1) {
+                            const int e = __shfl_sync(0xffffffffu, excl, src + st);
+                            if (e <= t) src += st;
+                        }
+                        const unsigned sme = __shfl_sync(0xffffffffu, me, src);
+                        const unsigned smo = __shfl_sync(0xffffffffu, mo, src);
+                        const int scb = __shfl_sync(0xffffffffu, cb0, src);
+                        const int sst = __shfl_sync(0xffffffffu, cstep, src);
+                        int r = t - __shfl_sync(0xffffffffu, excl, src);
+                        if (t < T) {
+                            const int ne = __popc(sme);
+                            const bool odd = r >= ne;
+                            unsigned m = odd ? smo : sme;
+                            if (odd) r -= ne;
+                            int pbit = 0;                 // position of the r-th set bit of m
+#pragma unroll
+                            for (int wdt = 16; wdt >= 1; wdt >>= 1) {
+                                const int lo = __popc(m & ((1u << wdt) - 1u));
+                                if (r >= lo) {
+                                    r -= lo;
+                                    m >>= wdt;
+                                    pbit += wdt;
+                                }
+                            }
+                            c = scb + sst * pbit + (odd ? 1 : 0);
+                            lit = true;
+                        }
+                    }
+                    push(c, lit);
                 }
 #if VRC_MERGE_LEFTOVERS
                 // the warps' leftover lit cells (fewer than 32 each) of this shell: published,
@@ -791,7 +908,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
 size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
     return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
-           (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32) * 4 + (size_t)nw * 4;
+           (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32 + 1) * 4 + (size_t)nw * 4;
 }
 
 // Radius stage, one thread per record after the record kernel (its FP64 work would
