@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include "vrc_internal.cuh"
@@ -143,15 +144,53 @@ float bits_as_float(int v) {
 // triangle covers (and a margin for rounding and for the widened triangle test) lands in
 // a cell that lists it.  Entries of a cell are sorted by a lower bound of the triangle's
 // distance to the light (distance from the light to the triangle's bounding box).
+// Each cell also records that bound for its first entry, and the covered distance: the
+// smallest, over the cell's triangles that every direction of the cell crosses (the four
+// corner rays hit it with barycentrics at least 1e-3 inside its edges, at least 0.06 degrees
+// off its plane), of the largest corner hit distance, padded for the float ray test.
 struct LightBufHost {
-    std::vector<int> start;
+    std::vector<int4> cell;
     std::vector<int2> ent;
 };
+
+// Whether the four corner rays from the light (directions dir, not normalised) all cross
+// triangle T (vertices relative to the light) well inside it; hmax gets the largest hit
+// distance.  Double precision.
+static bool covers_cell(const double q[3][3], const double dir[4][3], double& hmax) {
+    const double mb = 1e-3;
+    double e1[3], e2[3], nrm[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = q[1][k] - q[0][k];
+        e2[k] = q[2][k] - q[0][k];
+    }
+    nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    if (!(nn > 0.0)) return false;
+    hmax = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        const double* d = dir[c];
+        const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (std::fabs(d[0] * nrm[0] + d[1] * nrm[1] + d[2] * nrm[2]) < 1e-3 * dn * nn) return false;
+        double p[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
+        const double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+        const double s[3] = {-q[0][0], -q[0][1], -q[0][2]};       // the light relative to vertex 0
+        const double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) / det;
+        const double qv[3] = {s[1] * e1[2] - s[2] * e1[1], s[2] * e1[0] - s[0] * e1[2], s[0] * e1[1] - s[1] * e1[0]};
+        const double v = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) / det;
+        const double t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) / det;
+        if (!(u >= mb && v >= mb && u + v <= 1.0 - mb && t > 0.0)) return false;
+        hmax = std::max(hmax, t * dn);
+    }
+    return true;
+}
 
 void build_light_buffer(const std::vector<std::array<double, 9>>& tv, const std::vector<int>& bvh_index,
                         const double L[3], int R, LightBufHost& out) {
     const int ncell = 6 * R * R;
     std::vector<std::vector<std::pair<float, int>>> cells(ncell);
+    std::vector<int> orig(tv.size());                 // BVH leaf order -> triangle
     const double pad = 1e-4;
     for (size_t t = 0; t < tv.size(); ++t) {
         double q[3][3];
@@ -162,6 +201,7 @@ void build_light_buffer(const std::vector<std::array<double, 9>>& tv, const std:
                 lo[k] = std::min(lo[k], tv[t][3 * v + k]);
                 hi[k] = std::max(hi[k], tv[t][3 * v + k]);
             }
+        orig[bvh_index[t]] = (int)t;
         double dd = 0.0;
         for (int k = 0; k < 3; ++k) {
             double e = std::max(std::max(lo[k] - L[k], L[k] - hi[k]), 0.0);
@@ -209,22 +249,46 @@ void build_light_buffer(const std::vector<std::array<double, 9>>& tv, const std:
                 for (int j = j0; j <= j1; ++j) cells[(face * R + i) * R + j].push_back({dmin, bvh_index[t]});
         }
     }
-    out.start.assign(ncell + 1, 0);
+    out.cell.assign(ncell, make_int4(0, 0, 0, 0));
     size_t total = 0;
-    for (int c = 0; c < ncell; ++c) {
-        out.start[c] = (int)total;
-        total += cells[c].size();
-    }
-    out.start[ncell] = (int)total;
+    for (int c = 0; c < ncell; ++c) total += cells[c].size();
     out.ent.resize(total);
+    const float inf = std::numeric_limits<float>::infinity();
+    size_t at = 0;
     for (int c = 0; c < ncell; ++c) {
         auto& v = cells[c];
         std::sort(v.begin(), v.end());
         for (size_t k = 0; k < v.size(); ++k) {
             int bits;
             std::memcpy(&bits, &v[k].first, sizeof(bits));
-            out.ent[out.start[c] + k] = make_int2(v[k].second, bits);
+            out.ent[at + k] = make_int2(v[k].second, bits);
         }
+        // corner directions of the cell: major axis +-1, the next two axes at the cell's edges
+        const int face = c / (R * R), i = (c / R) % R, j = c % R;
+        const int axis = face / 2, ia = (axis + 1) % 3, ib = (axis + 2) % 3;
+        const double sg = (face & 1) ? -1.0 : 1.0;
+        double dir[4][3];
+        for (int k = 0; k < 4; ++k) {
+            dir[k][axis] = sg;
+            dir[k][ia] = 2.0 * (i + (k & 1)) / R - 1.0;
+            dir[k][ib] = 2.0 * (j + (k >> 1)) / R - 1.0;
+        }
+        double dsh = std::numeric_limits<double>::infinity();
+        for (size_t k = 0; k < v.size() && (double)v[k].first < dsh; ++k) {
+            const auto& T = tv[orig[v[k].second]];
+            double q[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) q[a][b] = T[3 * a + b] - L[b];
+            double hmax;
+            if (covers_cell(q, dir, hmax)) dsh = std::min(dsh, hmax * (1.0 + 1e-4) + 1e-5);
+        }
+        float dfirst = v.empty() ? inf : v[0].first;
+        float fsh = std::isinf(dsh) ? inf : std::nextafter((float)dsh, inf);
+        int bf, bs;
+        std::memcpy(&bf, &dfirst, sizeof(bf));
+        std::memcpy(&bs, &fsh, sizeof(bs));
+        out.cell[c] = make_int4((int)at, (int)(at + v.size()), bf, bs);
+        at += v.size();
     }
 }
 
@@ -333,8 +397,13 @@ extern "C" int vrc_build_scene(const float* verts, int32_t n_verts, const int32_
     if (!s) return VRC_ERR_OOM;
     int rc = VRC_OK;
     for (int l = 0; l < n_lights; ++l) {
-        if (lbs[l].start.empty()) lbs[l].start.assign(6 * lbR * lbR + 1, 0);
-        if ((rc = upload((void**)&s->d_lb_start[l], lbs[l].start.data(), lbs[l].start.size() * sizeof(int))) ||
+        if (lbs[l].cell.empty()) {
+            const float inf = std::numeric_limits<float>::infinity();
+            int bi;
+            std::memcpy(&bi, &inf, sizeof(bi));
+            lbs[l].cell.assign(6 * lbR * lbR, make_int4(0, 0, bi, bi));
+        }
+        if ((rc = upload((void**)&s->d_lb_cell[l], lbs[l].cell.data(), lbs[l].cell.size() * sizeof(int4))) ||
             (rc = upload((void**)&s->d_lb_ent[l], lbs[l].ent.data(), lbs[l].ent.size() * sizeof(int2)))) {
             vrc_destroy_scene(s);
             return rc;
@@ -362,7 +431,7 @@ extern "C" int vrc_build_scene(const float* verts, int32_t n_verts, const int32_
     for (int l = 0; l < n_lights; ++l) {
         d.lpos[l] = make_float3(lights[l].pos[0], lights[l].pos[1], lights[l].pos[2]);
         d.lI[l] = make_float3(lights[l].intensity[0], lights[l].intensity[1], lights[l].intensity[2]);
-        d.lb[l].start = s->d_lb_start[l];
+        d.lb[l].cell = s->d_lb_cell[l];
         d.lb[l].ent = s->d_lb_ent[l];
         d.lb[l].R = lbR;
     }
@@ -390,7 +459,7 @@ extern "C" void vrc_destroy_scene(vrc_scene* s) {
     cudaFree(s->d_pre_Lo);
     cudaFree(s->h_stage_dev);
     for (int l = 0; l < VRC_MAX_LIGHTS; ++l) {
-        cudaFree(s->d_lb_start[l]);
+        cudaFree(s->d_lb_cell[l]);
         cudaFree(s->d_lb_ent[l]);
     }
     std::free(s);

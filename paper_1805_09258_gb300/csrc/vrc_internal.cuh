@@ -25,7 +25,10 @@
 // overlaps the cell, sorted by that distance.  A shadow segment from y to the light can
 // only meet triangles listed in the cell of direction y - light that are nearer than y.
 struct DevLightBuf {
-    const int* __restrict__ start;      // [6 R R + 1]
+    // per cell: first and one-past-last entry, then float bits of (a) the first entry's
+    // distance bound (+inf for an empty cell) and (b) a distance beyond which every point
+    // of the cell is behind one triangle that covers the whole cell (+inf if none does)
+    const int4* __restrict__ cell;      // [6 R R]
     const int2* __restrict__ ent;       // (tri, float bits of the distance bound)
     int R;
 };
@@ -47,7 +50,7 @@ struct vrc_scene {
     float4* d_nodes;
     float4* d_tris;
     float4* d_prim;
-    int* d_lb_start[VRC_MAX_LIGHTS];
+    int4* d_lb_cell[VRC_MAX_LIGHTS];
     int2* d_lb_ent[VRC_MAX_LIGHTS];
     long long lb_entries;
     int n_prims;
@@ -287,13 +290,19 @@ __device__ __forceinline__ int lightbuf_cell(float3 w, int R) {
 }
 
 // Any hit on the segment from o toward light l (unit direction ld, length dist): the same
-// triangle test as bvh_trace<true>, over the light-buffer candidates nearer than o.
+// triangle test as bvh_trace<true>, over the light-buffer candidates nearer than o.  Two
+// per-cell bounds settle most points with one load and give the loop's own answer: a point
+// no further than the first candidate's bound is lit (the loop would stop there), and a
+// point beyond the covered distance is behind a triangle that every direction of the cell
+// crosses well inside its edges (the loop would find it, or an earlier hit).
 __device__ __forceinline__ bool lightbuf_occluded(const DevScene& sc, int l, float3 o, float3 ld, float dist) {
     const DevLightBuf& L = sc.lb[l];
     float3 w = o - sc.lpos[l];
     int c = lightbuf_cell(w, L.R);
-    int b = __ldg(&L.start[c]), e = __ldg(&L.start[c + 1]);
-    for (int p = b; p < e; ++p) {
+    const int4 cd = __ldg(&L.cell[c]);
+    if (!(dist > __int_as_float(cd.z))) return false;
+    if (dist > __int_as_float(cd.w)) return true;
+    for (int p = cd.x; p < cd.y; ++p) {
         int2 en = __ldg(&L.ent[p]);
         if (__int_as_float(en.y) >= dist) break;
         float t;
