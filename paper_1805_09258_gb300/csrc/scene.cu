@@ -143,11 +143,12 @@ float bits_as_float(int v) {
 // the clipped polygon onto a convex polygon inside that rectangle, so every direction the
 // triangle covers (and a margin for rounding and for the widened triangle test) lands in
 // a cell that lists it.  Entries of a cell are sorted by a lower bound of the triangle's
-// distance to the light (distance from the light to the triangle's bounding box).
-// Each cell also records that bound for its first entry, and the covered distance: the
-// smallest, over the cell's triangles that every direction of the cell crosses (the four
-// corner rays hit it with barycentrics at least 1e-3 inside its edges, at least 0.06 degrees
-// off its plane), of the largest corner hit distance, padded for the float ray test.
+// distance to the light: the larger of the distance to its bounding box and its distance
+// inside the cell's padded frustum (a triangle with no part there is left out).  Each cell
+// also records the bound of its first entry, and the covered distance: the smallest, over the
+// cell's triangles that every direction of the cell crosses (the four corner rays hit it with
+// barycentrics at least 1e-3 inside its edges, at least 0.06 degrees off its plane), of the
+// largest corner hit distance, padded for the float ray test.
 struct LightBufHost {
     std::vector<int4> cell;
     std::vector<int2> ent;
@@ -183,6 +184,80 @@ static bool covers_cell(const double q[3][3], const double dir[4][3], double& hm
         if (!(u >= mb && v >= mb && u + v <= 1.0 - mb && t > 0.0)) return false;
         hmax = std::max(hmax, t * dn);
     }
+    return true;
+}
+
+// The part of triangle T (vertices as (m, a, b) relative to the light) inside the frustum
+// u0 <= a/m <= u1, v0 <= b/m <= v1: false if none, else md gets its distance to the light.
+// Double precision.
+static bool cell_distance(const double T[3][3], double u0, double u1, double v0, double v1, double& md) {
+    double P[12][3], Q[12][3];
+    int n = 3;
+    for (int v = 0; v < 3; ++v)
+        for (int k = 0; k < 3; ++k) P[v][k] = T[v][k];
+    // half-spaces a - u0 m >= 0, u1 m - a >= 0, b - v0 m >= 0, v1 m - b >= 0
+    const double pl[4][3] = {{-u0, 1, 0}, {u1, -1, 0}, {-v0, 0, 1}, {v1, 0, -1}};
+    for (int p = 0; p < 4 && n > 0; ++p) {
+        int o = 0;
+        for (int i = 0; i < n; ++i) {
+            const double* A = P[i];
+            const double* B = P[(i + 1) % n];
+            double da = pl[p][0] * A[0] + pl[p][1] * A[1] + pl[p][2] * A[2];
+            double db = pl[p][0] * B[0] + pl[p][1] * B[1] + pl[p][2] * B[2];
+            if (da >= 0) {
+                for (int k = 0; k < 3; ++k) Q[o][k] = A[k];
+                ++o;
+            }
+            if ((da >= 0) != (db >= 0)) {
+                double s2 = da / (da - db);
+                for (int k = 0; k < 3; ++k) Q[o][k] = A[k] + s2 * (B[k] - A[k]);
+                ++o;
+            }
+        }
+        n = o;
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) P[i][k] = Q[i][k];
+    }
+    if (n == 0) return false;
+    // nearest point of the convex polygon to the light: the foot of the perpendicular when it
+    // falls inside, else the nearest point of an edge
+    double e1[3], e2[3], nr[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = T[1][k] - T[0][k];
+        e2[k] = T[2][k] - T[0][k];
+    }
+    nr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double nn = nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2];
+    double best = 1e300;
+    if (nn > 0.0 && n >= 3) {
+        const double h = (nr[0] * T[0][0] + nr[1] * T[0][1] + nr[2] * T[0][2]) / nn;
+        const double f[3] = {h * nr[0], h * nr[1], h * nr[2]};
+        bool pos = true, neg = true;
+        for (int i = 0; i < n; ++i) {
+            const double* A = P[i];
+            const double* B = P[(i + 1) % n];
+            double ex[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+            double fx[3] = {f[0] - A[0], f[1] - A[1], f[2] - A[2]};
+            double c = nr[0] * (ex[1] * fx[2] - ex[2] * fx[1]) + nr[1] * (ex[2] * fx[0] - ex[0] * fx[2]) +
+                       nr[2] * (ex[0] * fx[1] - ex[1] * fx[0]);
+            if (c < 0) pos = false;
+            if (c > 0) neg = false;
+        }
+        if (pos || neg) best = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    }
+    for (int i = 0; i < n; ++i) {
+        const double* A = P[i];
+        const double* B = P[(i + 1) % n];
+        double ex[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double ee = ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2];
+        double s2 = ee > 0.0 ? -(A[0] * ex[0] + A[1] * ex[1] + A[2] * ex[2]) / ee : 0.0;
+        s2 = std::min(1.0, std::max(0.0, s2));
+        double x[3] = {A[0] + s2 * ex[0], A[1] + s2 * ex[1], A[2] + s2 * ex[2]};
+        best = std::min(best, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+    }
+    md = best;
     return true;
 }
 
@@ -245,8 +320,25 @@ void build_light_buffer(const std::vector<std::array<double, 9>>& tv, const std:
             if (apex) { umin = vmin = -1.0; umax = vmax = 1.0; }
             auto cidx = [&](double u) { return std::min(R - 1, std::max(0, (int)std::floor((u + 1.0) * 0.5 * R))); };
             int i0 = cidx(umin - pad), i1 = cidx(umax + pad), j0 = cidx(vmin - pad), j1 = cidx(vmax + pad);
+            double tri[3][3];
+            for (int v = 0; v < 3; ++v) {
+                tri[v][0] = sg * q[v][axis];
+                tri[v][1] = q[v][ia];
+                tri[v][2] = q[v][ib];
+            }
             for (int i = i0; i <= i1; ++i)
-                for (int j = j0; j <= j1; ++j) cells[(face * R + i) * R + j].push_back({dmin, bvh_index[t]});
+                for (int j = j0; j <= j1; ++j) {
+                    // the triangle within the cell's padded frustum: no part, no entry; else
+                    // its distance there, less a margin for the widened float ray test, is
+                    // the entry's bound when it beats the bounding-box one
+                    double md;
+                    if (!cell_distance(tri, 2.0 * i / R - 1.0 - pad, 2.0 * (i + 1) / R - 1.0 + pad,
+                                       2.0 * j / R - 1.0 - pad, 2.0 * (j + 1) / R - 1.0 + pad, md))
+                        continue;
+                    float bd = (float)(md * (1.0 - 1e-5) - 1e-6);
+                    bd = std::nextafter(bd, 0.0f);
+                    cells[(face * R + i) * R + j].push_back({std::max(dmin, bd), bvh_index[t]});
+                }
         }
     }
     out.cell.assign(ncell, make_int4(0, 0, 0, 0));
