@@ -955,13 +955,15 @@ __global__ void k_radius(RecArgs a) {
 // and the surface radiance with its shadow rays, written for the record kernel to load.
 // As a flat launch it keeps every warp slot of the SM busy; inside the record kernel the
 // same traversal ran with two blocks per SM between barriers, at about half the rate.
-// Slots are pre_stride rays wide; a smaller ray set leaves the rest of its slot unused.
+// Slots are pre_stride rays wide (a multiple of 32); a smaller ray set leaves the rest of
+// its slot unused.
 // 12 blocks of 128 per SM (at most 42 registers): measured 3 % faster on a 2,048-triangle
 // scene and 8 % on a 250,000-triangle one than the unconstrained 70 registers
 __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
     // a batch holds at most PRE_MAX_RAYS (< 2^31) rays: 32-bit index arithmetic
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = (int)(i / (unsigned)a.pre_stride), gv = (int)(i - (unsigned)slot * (unsigned)a.pre_stride);
+    const int slot = (int)(i / (unsigned)a.pre_stride);
+    int gv = (int)(i - (unsigned)slot * (unsigned)a.pre_stride);
     const int item = a.item_base + slot;
     if (item >= a.item_end) return;
     const int rec = a.order ? a.order[item] : item;
@@ -969,6 +971,13 @@ __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, flo
     if (a.n_bands && (nb < 2 || nb > a.nb0)) return;        // flagged by the record kernel
     const int ns = a.n_bands ? 2 * nb : a.ns0;
     if (gv >= nb * ns + 2) return;
+    if (gv < nb * ns && (nb & 3) == 0 && (ns & 7) == 0) {
+        // a warp (slots are a multiple of 32 rays wide) traces a 4 x 8 tile of strata, not
+        // 32 bins of one band: neighbouring directions take similar paths through the BVH
+        const int tile = gv >> 5, w = gv & 31, tpr = ns >> 3;
+        const int bg = tile / tpr, bt = tile - bg * tpr;
+        gv = (4 * bg + (w >> 3)) * ns + 8 * bt + (w & 7);
+    }
     const float3 x = f3(a.pos[3 * rec], a.pos[3 * rec + 1], a.pos[3 * rec + 2]);
     const float3 d = ray_direction_dev(a.seed, a.rec_base + rec, gv, nb, ns);
     float th;
@@ -981,10 +990,11 @@ __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, flo
     } else {
         te = cube_exit_dev(x, d);
     }
-    ray[i] = make_float4(d.x, d.y, d.z, te);
-    Lo_out[3 * i] = Lo.x;
-    Lo_out[3 * i + 1] = Lo.y;
-    Lo_out[3 * i + 2] = Lo.z;
+    const unsigned at = (unsigned)slot * (unsigned)a.pre_stride + (unsigned)gv;   // the ray's own place
+    ray[at] = make_float4(d.x, d.y, d.z, te);
+    Lo_out[3 * at] = Lo.x;
+    Lo_out[3 * at + 1] = Lo.y;
+    Lo_out[3 * at + 2] = Lo.z;
     if (a.out.hit_prim) {
         size_t o = (size_t)rec * a.out.dbg_stride + gv;
         a.out.hit_prim[o] = prim;
@@ -1193,7 +1203,7 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.parts = p->parts;
     a.pre_ray = nullptr;
     a.pre_Lo = nullptr;
-    a.pre_stride = nb * ns + 2;                       // the largest ray set of the launch
+    a.pre_stride = (nb * ns + 2 + 31) & ~31;          // the largest ray set of the launch, whole warps
     a.item_base = 0;
     a.item_end = n;
     if (!s->tuning.no_prepass) {
@@ -1275,7 +1285,8 @@ extern "C" int vrc_records_graph_create(vrc_scene* s, const float* d_pos, int32_
         if (rc != VRC_OK) return rc;
     }
     if (!s->tuning.no_prepass) {
-        const long long stride = d_n_bands ? 2ll * p->n_bands * p->n_bands + 2 : (long long)p->n_bands * p->n_bins + 2;
+        const long long stride =
+            ((d_n_bands ? 2ll * p->n_bands * p->n_bands + 2 : (long long)p->n_bands * p->n_bins + 2) + 31) & ~31ll;
         long long rays = (long long)n * stride;
         if (rays > PRE_MAX_RAYS) rays = PRE_MAX_RAYS / stride * stride;
         if (rays < stride) rays = stride;
