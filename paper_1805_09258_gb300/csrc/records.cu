@@ -476,7 +476,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
             const bool north = r0 == 0, south = r1 == nb;
             const int nvert = rows * ns + 2;
             const int PN = rows * ns, PS = rows * ns + 1;
-            if (tid == 0) misc[0] = 0;
+            if (tid == 0) {
+                misc[0] = 0;
+                misc[2] = 0;
+            }
             __syncthreads();
             // ---------------- primary phase
             float tmax_loc = 0.f;
@@ -539,45 +542,14 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
             // cells of this chunk
             const int nq = r1e - r0;                         // quad bands with upper row in [r0, r1e)
             const int ncell = (north ? ns : 0) + 2 * ns * nq + (south ? ns : 0);
-            // Shell k's cell phase reads radiance buffer k & 1 while the same phase computes
-            // shell k + 1's vertex radiance into the other buffer: one barrier per shell, and
-            // the shadow-ray latency of some warps overlaps the cell arithmetic of others.
+            // Shell k's cell phase reads radiance buffer k & 1 while the same interval computes
+            // shell k + 1's vertex radiance into the other buffer, and the shadow-ray latency of
+            // some warps overlaps the cell arithmetic of others.
             for (int k = 0; k <= K; ++k) {
                 const float tk = ((float)k - 0.5f) * a.dt;
                 const float* Lrk = Lr + (k & 1) * (3 * a.cap);
                 const float* Lgk = Lrk + a.cap;
                 const float* Lbk = Lgk + a.cap;
-                if (k + 1 <= K) {
-                    // ---------------- vertex phase of medium shell k + 1
-                    const float tn = ((float)(k + 1) - 0.5f) * a.dt;
-                    float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
-                    unsigned* litn = litm + ((k + 1) & 1) * LW;
-                    const int nvround = (nvert + 31) & ~31;
-                    for (int vb = warp * 32; vb < nvround; vb += NT) {
-                        const int lv = vb + lane;
-                        bool lit_v = false;
-                        if (lv < nvert) {
-                        float4 rv = ray[lv];
-                        float3 d = f3(rv.x, rv.y, rv.z);
-                        float3 Lo = f3(0.f, 0.f, 0.f);
-                        if (tn < rv.w) {
-                            Lo = medium_radiance(sc, x + d * tn, d);
-                            if (lv < (r1 - r0) * ns) {                // a vertex of an owned row
-                                float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * tn);
-                                neumaier(mc[3], mcc[3], w * Lo.x);
-                                neumaier(mc[4], mcc[4], w * Lo.y);
-                                neumaier(mc[5], mcc[5], w * Lo.z);
-                            }
-                        }
-                        Lrn[lv] = Lo.x;
-                        Lrn[a.cap + lv] = Lo.y;
-                        Lrn[2 * a.cap + lv] = Lo.z;
-                        lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
-                        }
-                        unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
-                        if (lane == 0) litn[vb >> 5] = lmk;
-                    }
-                }
                 // ---------------- cell phase of shell k: lit cells are compacted into a
                 // per-warp queue so cell_eval runs with all 32 lanes busy
                 auto cell_verts = [&](int cc, int (&vi)[3]) {
@@ -792,12 +764,58 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     push(c, lit);
                 }
 #if VRC_MERGE_LEFTOVERS
+                if (k + 1 <= K) {
+                    // ---------------- vertex phase of medium shell k + 1, after this shell's
+                    // scan: batches of 32 vertices handed out by a counter, so the warps that
+                    // ran no cell batches take more of them (each vertex's radiance does not
+                    // depend on who computes it; the Monte Carlo sums are taken after the
+                    // barrier, in a fixed order)
+                    const float tn = ((float)(k + 1) - 0.5f) * a.dt;
+                    float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
+                    unsigned* litn = litm + ((k + 1) & 1) * LW;
+                    const int nbat = (nvert + 31) >> 5;
+                    for (;;) {
+                        int vb = 0;
+                        if (lane == 0) vb = atomicAdd(&misc[2], 1);
+                        vb = __shfl_sync(0xffffffffu, vb, 0);
+                        if (vb >= nbat) break;
+                        const int lv = vb * 32 + lane;
+                        bool lit_v = false;
+                        if (lv < nvert) {
+                            const float4 rv = ray[lv];
+                            float3 Lo = f3(0.f, 0.f, 0.f);
+                            if (tn < rv.w) Lo = medium_radiance(sc, x + f3(rv.x, rv.y, rv.z) * tn, f3(rv.x, rv.y, rv.z));
+                            Lrn[lv] = Lo.x;
+                            Lrn[a.cap + lv] = Lo.y;
+                            Lrn[2 * a.cap + lv] = Lo.z;
+                            lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
+                        }
+                        const unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
+                        if (lane == 0) litn[vb] = lmk;
+                    }
+                }
                 // the warps' leftover lit cells (fewer than 32 each) of this shell: published,
                 // then processed as one warp-major list, a full chunk of 32 per warp, instead
                 // of one partly idle call per warp (the order is fixed: results stay
                 // deterministic)
                 if (lane == 0) wcnt[warp] = qn;
                 __syncthreads();
+                if (tid == 0) misc[2] = 0;                    // the next interval's vertex batches
+                if (k + 1 <= K) {
+                    // Monte Carlo terms of shell k + 1's owned vertices, a fixed set per thread
+                    const float tn = ((float)(k + 1) - 0.5f) * a.dt;
+                    const float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
+                    const float wsh = wmc * __expf(-sigma_t * tn);
+                    for (int lv = tid; lv < (r1 - r0) * ns; lv += NT) {
+                        const float4 rv = ray[lv];
+                        if (tn < rv.w) {
+                            const float w = wsh * hg_dev(-(rv.x * a.wo.x + rv.y * a.wo.y + rv.z * a.wo.z), g);
+                            neumaier(mc[3], mcc[3], w * Lrn[lv]);
+                            neumaier(mc[4], mcc[4], w * Lrn[a.cap + lv]);
+                            neumaier(mc[5], mcc[5], w * Lrn[2 * a.cap + lv]);
+                        }
+                    }
+                }
                 {
                     int tot = 0, src = -1;
                     const int t = warp * 32 + lane;
