@@ -386,9 +386,6 @@ __device__ __noinline__ void write_ellipsoid(const double h[6], const double lam
 // chunk sized so three blocks' shared memory fits too.  The cell arithmetic spills a little
 // at this cap, but the extra warps hide the latency of the rest: measured 7 % faster on the
 // mid workload and 11 % on the render one than 2 blocks at 128 registers.
-#ifndef VRC_MERGE_LEFTOVERS
-#define VRC_MERGE_LEFTOVERS 1
-#endif
 #ifndef VRC_RECORDS_REGS
 #define VRC_RECORDS_REGS 85
 #endif
@@ -602,20 +599,21 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     else neumaier(acc_m, cmp_m, mine);
                 };
                 int* wqw = wq + warp * 64;
-                int qn = 0;
+                int qn = 0, qb = 0;                      // queue length; its first slot
                 const unsigned* lmk = litm + (k & 1) * LW;
-                // appends the lanes' lit cells to the warp's queue; a full queue runs cell_eval
-                auto push = [&](int c, bool lit) {
+                // appends the lanes' lit cells to the warp's queue; a full queue (or a flush)
+                // runs cell_eval
+                auto push = [&](int c, bool lit, bool flush) {
                     unsigned msk = __ballot_sync(0xffffffffu, lit);
-                    if (lit) wqw[qn + __popc(msk & ((1u << lane) - 1u))] = c;
+                    if (lit) wqw[qb + qn + __popc(msk & ((1u << lane) - 1u))] = c;
                     qn += __popc(msk);
                     __syncwarp();
-                    if (qn >= 32) {
-                        process(wqw[lane]);
+                    if (qn >= 32 || (flush && qn > 0)) {
+                        process(lane < qn ? wqw[qb + lane] : -1);
                         __syncwarp();
-                        if (lane < qn - 32) wqw[lane] = wqw[lane + 32];
+                        if (lane < qn - 32) wqw[qb + lane] = wqw[qb + lane + 32];
                         __syncwarp();
-                        qn -= 32;
+                        qn = qn > 32 ? qn - 32 : 0;
                     }
                 };
                 // One loop, one push site (cell_eval is inlined once).  Surface shell: a cell
@@ -639,10 +637,21 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 int sb = 0, rb0 = 0, T = 0, excl = 0;    // medium shells: segment pass, step, lit count
                 unsigned me = 0u, mo = 0u;               // this lane's lit even / odd cells (fans: me)
                 int cb0 = 0, cstep = 1;                  // cell of bit p: cb0 + cstep p (+ 1 if odd)
+                int src = -1;                            // pass 1: this lane's merged leftover cell
+                bool merged = false;
+                // pass 0 scans the shell; pass 1 runs the warp's share of the merged leftovers
+                // through the same push (one call site, so cell_eval is inlined once)
+#pragma unroll 1
+                for (int pass = 0; pass < 2; ++pass) {
                 for (;;) {
                     int c = -1;
                     bool lit = false;
-                    if (k == 0) {
+                    if (pass == 1) {
+                        if (merged) break;
+                        merged = true;
+                        c = src;
+                        lit = src >= 0;
+                    } else if (k == 0) {
                         if (base >= nround) break;
                         c = base + lane;
                         base += NT;
@@ -761,9 +770,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                             lit = true;
                         }
                     }
-                    push(c, lit);
+                    push(c, lit, pass == 1);
                 }
-#if VRC_MERGE_LEFTOVERS
+                if (pass == 1) break;
                 if (k + 1 <= K) {
                     // ---------------- vertex phase of medium shell k + 1, after this shell's
                     // scan: batches of 32 vertices handed out by a counter, so the warps that
@@ -817,7 +826,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     }
                 }
                 {
-                    int tot = 0, src = -1;
+                    int tot = 0;
                     const int t = warp * 32 + lane;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) {
@@ -825,15 +834,13 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         if (src < 0 && t >= tot && t < tot + cw) src = wq[w * 64 + (t - tot)];
                         tot += cw;
                     }
-                    if (warp * 32 < tot) process(src);      // src -1: an idle lane
-                    __syncwarp();
+                    // the published leftovers (slots below 32) may still be read by other
+                    // warps: the merged chunk goes through the upper half of the queue
+                    qn = 0;
+                    qb = 32;
+                    if (warp * 32 >= tot) break;     // src -1 lanes: idle in the merged chunk
                 }
-#else
-                if (qn > 0) {
-                    process(lane < qn ? wqw[lane] : -1);
-                    __syncwarp();
                 }
-#endif
                 __syncthreads();
             }
         }
