@@ -150,9 +150,11 @@ typedef struct {
     float* axes;
 } vrc_records_view;
 
-/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default. */
+/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default: 384
+ * threads with the whole ray set in shared memory when that fits two blocks per SM (up to
+ * 110 KB), else 256 threads with as many bands per chunk as fit 72 KB (three blocks). */
 typedef struct {
-    int32_t threads;        /* threads per block: 128, 256, 512 */
+    int32_t threads;        /* threads per block: 128, 256, 384, 512 */
     int32_t chunk_bands;    /* bands of the ray set kept in shared memory at once */
     int32_t blocks_per_sm;  /* persistent blocks per SM */
     int32_t shadow_bvh;     /* 1: shadow rays traverse the BVH; 0: light buffer (default) */
