@@ -984,6 +984,75 @@ __global__ void k_radius(RecArgs a) {
 // its slot unused.
 // 12 blocks of 128 per SM (at most 42 registers): measured 3 % faster on a 2,048-triangle
 // scene and 8 % on a 250,000-triangle one than the unconstrained 70 registers
+// Closest hit along o + t d (t > VRC_TMIN) for the pre-pass: the traversal of bvh_trace with
+// the inner-node and leaf steps in separate loops, so the lanes of a warp that reach a leaf
+// wait for the others and the warp tests its leaves together (node and triangle order per
+// ray, and so the result, are those of bvh_trace).
+__device__ int bvh_closest_ww(const DevScene& sc, float3 o, float3 d, float* t_hit) {
+    constexpr int DONE = (int)0x80000000;
+    const float big = 1e30f;
+    const float tmin = VRC_TMIN;
+    float best_t = 3.0e38f;
+    int best = -1;
+    if (sc.n_tris == 0) {
+        *t_hit = best_t;
+        return -1;
+    }
+    const float3 inv = f3(fabsf(d.x) > 1e-30f ? 1.0f / d.x : copysignf(big, d.x),
+                          fabsf(d.y) > 1e-30f ? 1.0f / d.y : copysignf(big, d.y),
+                          fabsf(d.z) > 1e-30f ? 1.0f / d.z : copysignf(big, d.z));
+    const float3 oi = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    int stack[VRC_STACK];
+    int sp = 0;
+    int code = 0;
+    for (;;) {
+        while (code >= 0) {
+            const float4* N = sc.nodes + 4 * code;
+            const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+            float a0 = fmaf(n0.x, inv.x, -oi.x), a1 = fmaf(n0.y, inv.x, -oi.x);
+            float b0 = fmaf(n0.z, inv.y, -oi.y), b1 = fmaf(n0.w, inv.y, -oi.y);
+            float z0 = fmaf(n2.x, inv.z, -oi.z), z1 = fmaf(n2.y, inv.z, -oi.z);
+            const float tn0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, b1)), fmaxf(fminf(z0, z1), tmin));
+            const float tf0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, b1)), fminf(fmaxf(z0, z1), best_t));
+            a0 = fmaf(n1.x, inv.x, -oi.x); a1 = fmaf(n1.y, inv.x, -oi.x);
+            b0 = fmaf(n1.z, inv.y, -oi.y); b1 = fmaf(n1.w, inv.y, -oi.y);
+            z0 = fmaf(n2.z, inv.z, -oi.z); z1 = fmaf(n2.w, inv.z, -oi.z);
+            const float tn1 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, b1)), fmaxf(fminf(z0, z1), tmin));
+            const float tf1 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, b1)), fminf(fmaxf(z0, z1), best_t));
+            const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            if (h0 && h1) {
+                const int nearc = tn0 <= tn1 ? c0 : c1, farc = tn0 <= tn1 ? c1 : c0;
+                if (sp < VRC_STACK) stack[sp++] = farc;
+                code = nearc;
+            } else if (h0) {
+                code = c0;
+            } else if (h1) {
+                code = c1;
+            } else {
+                code = sp == 0 ? DONE : stack[--sp];
+            }
+        }
+        if (code == DONE) break;
+        const int z = -code - 1;
+        const int first = z >> 3, count = (z & 7) + 1;
+        for (int k = first; k < first + count; ++k) {
+            float t;
+            int id;
+            if (tri_hit(sc.tris, k, o, d, tmin, best_t * (1.0f + 1e-7f) + 1e-30f, &t, &id)) {
+                if (t < best_t || (t == best_t && id < best)) {
+                    best_t = t;
+                    best = id;
+                }
+            }
+        }
+        code = sp == 0 ? DONE : stack[--sp];
+        if (code == DONE) break;
+    }
+    *t_hit = best_t;
+    return best;
+}
+
 __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, float4* ray, float* Lo_out) {
     // a batch holds at most PRE_MAX_RAYS (< 2^31) rays: 32-bit index arithmetic
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1006,7 +1075,9 @@ __global__ void __launch_bounds__(128, 12) k_primary(DevScene sc, RecArgs a, flo
     const float3 x = f3(a.pos[3 * rec], a.pos[3 * rec + 1], a.pos[3 * rec + 2]);
     const float3 d = ray_direction_dev(a.seed, a.rec_base + rec, gv, nb, ns);
     float th;
-    const int prim = bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
+    // measured: the separate leaf loop is 12 % faster on a 250,000-triangle scene and 0.8 %
+    // slower on a 2,048-triangle one (whose traversals are short)
+    const int prim = sc.n_tris > 16384 ? bvh_closest_ww(sc, x, d, &th) : bvh_trace<false>(sc, x, d, VRC_TMIN, 3.0e38f, &th);
     float3 Lo = f3(0.f, 0.f, 0.f);
     float te;
     if (prim >= 0) {

@@ -64,12 +64,14 @@ def test_mid_workload_full_size_sampled(vrc):
 
 
 def test_ragged_sizes_and_chunks(vrc):
-    """Odd band and bin counts, a ragged record count, and ray sets split into many chunks."""
+    """Odd band and bin counts, a ragged record count, and ray sets split into many chunks,
+    for every block size (the default keeps the whole ray set in one chunk)."""
     w = W.config2()
     rp = RecordParams(n_bands=13, n_bins=27)
     pos = w.positions(37, seed=77)
     ref = O.records(O.OracleScene(w.scene), rp, pos, track_margins=1)
-    for tuning in (None, dict(threads=128, chunk_bands=3), dict(threads=512, chunk_bands=5)):
+    for tuning in (None, dict(threads=128, chunk_bands=3), dict(threads=256), dict(threads=384, chunk_bands=4),
+                   dict(threads=512, chunk_bands=5)):
         g = run_gpu(vrc, w.scene, rp, pos, tuning=tuning)
         compare_records(g, ref)
         compare_radius(g, ref)
