@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
     const int LW = ((a.cap + 31) >> 5) + 1;                  // + 1: 32-bit windows may read one word past
     unsigned* litm = reinterpret_cast<unsigned*>(wq + NW * 64);   // [2][LW]: vertex has radiance (bit per vertex)
     int* wcnt = reinterpret_cast<int*>(litm + 2 * LW);            // [NW] leftover lit cells per warp
+    float* bmax = reinterpret_cast<float*>(wcnt + NW);            // [LW] furthest ray end per 32 vertices
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float sigma_t = sc.sigma_t, g = sc.g;
     __shared__ int s_rec, s_item;
@@ -484,6 +485,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
             for (int vb = warp * 32; vb < nvround; vb += NT) {
                 const int lv = vb + lane;
                 bool lit_v = false;
+                float te_b = 0.f;
                 if (lv < nvert) {
                 const bool pole = lv >= rows * ns;
                 const int gv = !pole ? r0 * ns + lv : (lv == PN ? N : N + 1);
@@ -516,6 +518,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 Lb[lv] = Lo.z;
                 lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
                 tmax_loc = fmaxf(tmax_loc, te);
+                te_b = te;
                 const bool owned = lv < (r1 - r0) * ns;        // a vertex of the rows this chunk owns
                 if (owned && prim >= 0) {
                     float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * te);
@@ -530,7 +533,12 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 }
             }
                 unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
-                if (lane == 0) litm[vb >> 5] = lmk;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) te_b = fmaxf(te_b, __shfl_xor_sync(0xffffffffu, te_b, o));
+                if (lane == 0) {
+                    litm[vb >> 5] = lmk;
+                    bmax[vb >> 5] = te_b;
+                }
             }
             atomicMax(&misc[0], __float_as_int(tmax_loc));   // non-negative floats order as ints
             __syncthreads();
@@ -788,6 +796,12 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         if (lane == 0) vb = atomicAdd(&misc[2], 1);
                         vb = __shfl_sync(0xffffffffu, vb, 0);
                         if (vb >= nbat) break;
+                        if (!(tn < bmax[vb])) {
+                            // every ray of the batch has ended: no radiance and no bits (a cell
+                            // reads the radiance of its furthest, open vertices only)
+                            if (lane == 0) litn[vb] = 0u;
+                            continue;
+                        }
                         const int lv = vb * 32 + lane;
                         bool lit_v = false;
                         if (lv < nvert) {
@@ -816,6 +830,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     const float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
                     const float wsh = wmc * __expf(-sigma_t * tn);
                     for (int lv = tid; lv < (r1 - r0) * ns; lv += NT) {
+                        if (!(tn < bmax[lv >> 5])) continue;    // the warp's 32 rays have ended
                         const float4 rv = ray[lv];
                         if (tn < rv.w) {
                             const float w = wsh * hg_dev(-(rv.x * a.wo.x + rv.y * a.wo.y + rv.z * a.wo.z), g);
@@ -933,7 +948,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
 size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
     return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
-           (size_t)nw * 64 * 4 + 2 * (size_t)((cap + 31) / 32 + 1) * 4 + (size_t)nw * 4;
+           (size_t)nw * 64 * 4 + 3 * (size_t)((cap + 31) / 32 + 1) * 4 + (size_t)nw * 4;
 }
 
 // Radius stage, one thread per record after the record kernel (its FP64 work would
