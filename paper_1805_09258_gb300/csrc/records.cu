@@ -407,6 +407,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
     unsigned* litm = reinterpret_cast<unsigned*>(wq + NW * 64);   // [2][LW]: vertex has radiance (bit per vertex)
     int* wcnt = reinterpret_cast<int*>(litm + 2 * LW);            // [NW] leftover lit cells per warp
     float* bmax = reinterpret_cast<float*>(wcnt + NW);            // [LW] furthest ray end per 32 vertices
+    float* bmc = bmax + LW;                                       // [LW][3] a batch's Monte Carlo sum
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float sigma_t = sc.sigma_t, g = sc.g;
     __shared__ int s_rec, s_item;
@@ -785,9 +786,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                     // ---------------- vertex phase of medium shell k + 1, after this shell's
                     // scan: batches of 32 vertices handed out by a counter, so the warps that
                     // ran no cell batches take more of them (each vertex's radiance does not
-                    // depend on who computes it; the Monte Carlo sums are taken after the
-                    // barrier, in a fixed order)
+                    // depend on who computes it, and each batch's Monte Carlo sum is taken in
+                    // a fixed lane order and added after the barrier in batch order)
                     const float tn = ((float)(k + 1) - 0.5f) * a.dt;
+                    const float wsh = wmc * __expf(-sigma_t * tn);
                     float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
                     unsigned* litn = litm + ((k + 1) & 1) * LW;
                     const int nbat = (nvert + 31) >> 5;
@@ -799,22 +801,41 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         if (!(tn < bmax[vb])) {
                             // every ray of the batch has ended: no radiance and no bits (a cell
                             // reads the radiance of its furthest, open vertices only)
-                            if (lane == 0) litn[vb] = 0u;
+                            if (lane == 0) {
+                                litn[vb] = 0u;
+                                bmc[3 * vb] = bmc[3 * vb + 1] = bmc[3 * vb + 2] = 0.f;
+                            }
                             continue;
                         }
                         const int lv = vb * 32 + lane;
                         bool lit_v = false;
+                        float3 term = f3(0.f, 0.f, 0.f);     // Monte Carlo term of an owned vertex
                         if (lv < nvert) {
                             const float4 rv = ray[lv];
                             float3 Lo = f3(0.f, 0.f, 0.f);
-                            if (tn < rv.w) Lo = medium_radiance(sc, x + f3(rv.x, rv.y, rv.z) * tn, f3(rv.x, rv.y, rv.z));
+                            if (tn < rv.w) {
+                                Lo = medium_radiance(sc, x + f3(rv.x, rv.y, rv.z) * tn, f3(rv.x, rv.y, rv.z));
+                                if (lv < (r1 - r0) * ns) term = Lo * (wsh * hg_dev(-(rv.x * a.wo.x + rv.y * a.wo.y + rv.z * a.wo.z), g));
+                            }
                             Lrn[lv] = Lo.x;
                             Lrn[a.cap + lv] = Lo.y;
                             Lrn[2 * a.cap + lv] = Lo.z;
                             lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
                         }
                         const unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
-                        if (lane == 0) litn[vb] = lmk;
+                        // the batch's Monte Carlo sum in a fixed lane order, whoever computes it
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) {
+                            term.x += __shfl_xor_sync(0xffffffffu, term.x, o);
+                            term.y += __shfl_xor_sync(0xffffffffu, term.y, o);
+                            term.z += __shfl_xor_sync(0xffffffffu, term.z, o);
+                        }
+                        if (lane == 0) {
+                            litn[vb] = lmk;
+                            bmc[3 * vb] = term.x;
+                            bmc[3 * vb + 1] = term.y;
+                            bmc[3 * vb + 2] = term.z;
+                        }
                     }
                 }
                 // the warps' leftover lit cells (fewer than 32 each) of this shell: published,
@@ -825,19 +846,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 __syncthreads();
                 if (tid == 0) misc[2] = 0;                    // the next interval's vertex batches
                 if (k + 1 <= K) {
-                    // Monte Carlo terms of shell k + 1's owned vertices, a fixed set per thread
-                    const float tn = ((float)(k + 1) - 0.5f) * a.dt;
-                    const float* Lrn = Lr + ((k + 1) & 1) * (3 * a.cap);
-                    const float wsh = wmc * __expf(-sigma_t * tn);
-                    for (int lv = tid; lv < (r1 - r0) * ns; lv += NT) {
-                        if (!(tn < bmax[lv >> 5])) continue;    // the warp's 32 rays have ended
-                        const float4 rv = ray[lv];
-                        if (tn < rv.w) {
-                            const float w = wsh * hg_dev(-(rv.x * a.wo.x + rv.y * a.wo.y + rv.z * a.wo.z), g);
-                            neumaier(mc[3], mcc[3], w * Lrn[lv]);
-                            neumaier(mc[4], mcc[4], w * Lrn[a.cap + lv]);
-                            neumaier(mc[5], mcc[5], w * Lrn[2 * a.cap + lv]);
-                        }
+                    // shell k + 1's batch sums, batch b into thread b % NT's compensated sums
+                    for (int b = tid; b < ((nvert + 31) >> 5); b += NT) {
+                        neumaier(mc[3], mcc[3], bmc[3 * b]);
+                        neumaier(mc[4], mcc[4], bmc[3 * b + 1]);
+                        neumaier(mc[5], mcc[5], bmc[3 * b + 2]);
                     }
                 }
                 {
@@ -948,7 +961,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
 size_t record_smem_bytes(int cap, int nt) {
     int nw = nt / 32;
     return (size_t)cap * 16 + (size_t)cap * 24 + (size_t)nw * 32 * 4 * 4 + (size_t)nw * 12 * 4 + 128 * 4 + 4 * 4 +
-           (size_t)nw * 64 * 4 + 3 * (size_t)((cap + 31) / 32 + 1) * 4 + (size_t)nw * 4;
+           (size_t)nw * 64 * 4 + 6 * (size_t)((cap + 31) / 32 + 1) * 4 + (size_t)nw * 4;
 }
 
 // Radius stage, one thread per record after the record kernel (its FP64 work would
