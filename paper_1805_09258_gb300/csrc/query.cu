@@ -211,31 +211,43 @@ __global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, c
                                                const int* __restrict__ cell_start, const int* __restrict__ list,
                                                int G, const float* __restrict__ q, const int* __restrict__ perm,
                                                int nq, float* __restrict__ rgb, int* __restrict__ status) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nq) return;
-    int i = perm[s];
-    float3 x = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
-    int c = cell_of(x, G);
-    int b = cell_start[c], e = cell_start[c + 1];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool active = s < nq;
+    const unsigned am = __ballot_sync(0xffffffffu, active);
+    if (am == 0u) return;                                // the whole warp is past the queries
+    int i = 0, c = 0;
+    float3 x = make_float3(0.f, 0.f, 0.f);
+    if (active) {
+        i = perm[s];
+        x = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+        c = cell_of(x, G);
+    }
+    // the warp's queries are binned by cell: when they all fall in one cell, its record rows
+    // are staged in shared memory 32 at a time by the lanes together, and every lane reads
+    // them from there (the same rows, in the same order, as the per-lane loop below)
+    const int c0 = __shfl_sync(0xffffffffu, c, __ffs(am) - 1);
+    const bool uniform = __all_sync(0xffffffffu, !active || c == c0);
+    const int b = cell_start[uniform ? c0 : c], e = cell_start[(uniform ? c0 : c) + 1];
     float ar = 0.f, ag = 0.f, ab = 0.f, sw = 0.f;
     int cnt = 0;
-    for (int p = b; p < e; ++p) {
-        int k = __ldg(&list[p]);
-        float4 a = __ldg(&rec[4 * k]);
+    // candidate record k with row `row` (its first float4 already in a)
+    auto candidate = [&](int k, float4 a, const float4* row, bool staged) {
         float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
         float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (!(d2 < a.w * a.w)) continue;
+        if (!(d2 < a.w * a.w)) return;
         float dd;
         if (ANISO) {
             float4 m0 = __ldg(&ell[2 * k]), m1 = __ldg(&ell[2 * k + 1]);
             float r2e = fmaf(m0.x * dx, dx, fmaf(m0.w * dy, dy, m1.y * dz * dz)) +
                         2.0f * fmaf(m0.y * dx, dy, fmaf(m0.z * dx, dz, m1.x * dy * dz));
-            if (!(r2e < 1.0f)) continue;
+            if (!(r2e < 1.0f)) return;
             dd = 1.0f - sqrtf(fmaxf(r2e, 0.f));
         } else {
             dd = 1.0f - sqrtf(d2) / a.w;
         }
-        float4 r1 = __ldg(&rec[4 * k + 1]), r2 = __ldg(&rec[4 * k + 2]), r3 = __ldg(&rec[4 * k + 3]);
+        const float4 r1 = staged ? row[1] : __ldg(row + 1), r2 = staged ? row[2] : __ldg(row + 2),
+                     r3 = staged ? row[3] : __ldg(row + 3);
         float w = dd * dd * fmaf(-2.0f, dd, 3.0f);
         float vr = r1.x + fmaf(r1.w, dx, fmaf(r2.x, dy, r2.y * dz));
         float vg = r1.y + fmaf(r2.z, dx, fmaf(r2.w, dy, r3.x * dz));
@@ -261,7 +273,32 @@ __global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, c
         ab = fmaf(w, vb, ab);
         sw += w;
         ++cnt;
+    };
+    if (uniform) {
+        __shared__ float4 rows[256 / 32][32][4];
+        __shared__ int ids[256 / 32][32];
+        float4(*rw)[4] = rows[threadIdx.x >> 5];
+        int* kw = ids[threadIdx.x >> 5];
+        for (int p0 = b; p0 < e; p0 += 32) {
+            const int n = min(32, e - p0);
+            if (lane < n) {
+                const int k = __ldg(&list[p0 + lane]);
+                kw[lane] = k;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) rw[lane][h] = __ldg(&rec[4 * k + h]);
+            }
+            __syncwarp();
+            if (active)
+                for (int j = 0; j < n; ++j) candidate(kw[j], rw[j][0], rw[j], true);
+            __syncwarp();
+        }
+    } else if (active) {
+        for (int p = b; p < e; ++p) {
+            const int k = __ldg(&list[p]);
+            candidate(k, __ldg(&rec[4 * k]), rec + 4 * k, false);
+        }
     }
+    if (!active) return;
     float inv = cnt ? 1.0f / sw : 0.0f;
     rgb[3 * i] = ar * inv;
     rgb[3 * i + 1] = ag * inv;
