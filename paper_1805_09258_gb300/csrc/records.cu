@@ -1181,7 +1181,8 @@ int launch_records(vrc_scene* s, const RecArgs& a0, size_t smem, cudaStream_t st
         kfn<<<grid, NT, smem, st>>>(dv, a);
     }
     if (ev) cudaEventRecord(ev[2], st);
-    k_radius<<<(a.n + 127) / 128, 128, 0, st>>>(a);
+    // one warp per block: a few thousand records then spread over every SM's FP64 units
+    k_radius<<<(a.n + 31) / 32, 32, 0, st>>>(a);
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
