@@ -198,10 +198,13 @@ __global__ void k_bin_queries(const float* q, int nq, int G, int* qcell, int* qr
     qrank[i] = atomicAdd(&counts[c], 1);
 }
 
-__global__ void k_scatter_queries(const int* qcell, const int* qrank, const int* start, int nq, int* perm) {
+// each query's point and index at its place in cell order (the query kernel then reads
+// them coalesced, without a dependent gather)
+__global__ void k_scatter_queries(const float* q, const int* qcell, const int* qrank, const int* start, int nq,
+                                  float4* pts) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nq) return;
-    perm[start[qcell[i]] + qrank[i]] = i;
+    pts[start[qcell[i]] + qrank[i]] = make_float4(q[3 * i], q[3 * i + 1], q[3 * i + 2], __int_as_float(i));
 }
 
 // one thread per query, in cell order
@@ -209,8 +212,8 @@ template <int ORDER, bool ANISO>
 __global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, const float4* __restrict__ hess,
                                                const float4* __restrict__ ell,
                                                const int* __restrict__ cell_start, const int* __restrict__ list,
-                                               int G, const float* __restrict__ q, const int* __restrict__ perm,
-                                               int nq, float* __restrict__ rgb, int* __restrict__ status) {
+                                               int G, const float4* __restrict__ pts, int nq,
+                                               float* __restrict__ rgb, int* __restrict__ status) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool active = s < nq;
@@ -219,8 +222,9 @@ __global__ void __launch_bounds__(256) k_query(const float4* __restrict__ rec, c
     int i = 0, c = 0;
     float3 x = make_float3(0.f, 0.f, 0.f);
     if (active) {
-        i = perm[s];
-        x = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+        const float4 p = pts[s];
+        i = __float_as_int(p.w);
+        x = make_float3(p.x, p.y, p.z);
         c = cell_of(x, G);
     }
     // the warp's queries are binned by cell: when they all fall in one cell, its record rows
@@ -327,7 +331,7 @@ extern "C" void vrc_destroy_grid(vrc_grid* g) {
     cudaFree(g->cell_list);
     cudaFree(g->q_cell);
     cudaFree(g->q_rank);
-    cudaFree(g->q_perm);
+    cudaFree(g->q_pts);
     cudaFree(g->q_count);
     cudaFree(g->scan_tmp);
     delete g;
@@ -472,10 +476,11 @@ extern "C" int vrc_query_inscatter(const vrc_grid* gc, const float* d_q, int32_t
     if (g->q_cap < nq) {
         cudaFree(g->q_cell);
         cudaFree(g->q_rank);
-        cudaFree(g->q_perm);
-        g->q_cell = g->q_rank = g->q_perm = nullptr;
+        cudaFree(g->q_pts);
+        g->q_cell = g->q_rank = nullptr;
+        g->q_pts = nullptr;
         g->q_cap = 0;
-        if (dev_alloc(&g->q_cell, nq) || dev_alloc(&g->q_rank, nq) || dev_alloc(&g->q_perm, nq)) return VRC_ERR_OOM;
+        if (dev_alloc(&g->q_cell, nq) || dev_alloc(&g->q_rank, nq) || dev_alloc(&g->q_pts, nq)) return VRC_ERR_OOM;
         g->q_cap = nq;
     }
     int G = g->G, ncell = G * G * G;
@@ -485,10 +490,10 @@ extern "C" int vrc_query_inscatter(const vrc_grid* gc, const float* d_q, int32_t
     // reuse cell_start-sized scratch: the query offsets go to q_count's scan in place
     int rc = exclusive_scan(g->q_count, ncell, g->q_count, g->scan_tmp, st);
     if (rc) return rc;
-    k_scatter_queries<<<nbk, tb, 0, st>>>(g->q_cell, g->q_rank, g->q_count, nq, g->q_perm);
+    k_scatter_queries<<<nbk, tb, 0, st>>>(d_q, g->q_cell, g->q_rank, g->q_count, nq, g->q_pts);
     auto kfn = g->order == 2 ? (g->aniso ? k_query<2, true> : k_query<2, false>)
                              : (g->aniso ? k_query<1, true> : k_query<1, false>);
-    kfn<<<nbk, tb, 0, st>>>(g->rec, g->hess, g->ell, g->cell_start, g->cell_list, G, d_q, g->q_perm, nq, d_rgb,
+    kfn<<<nbk, tb, 0, st>>>(g->rec, g->hess, g->ell, g->cell_start, g->cell_list, G, g->q_pts, nq, d_rgb,
                             d_status);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }

@@ -90,7 +90,7 @@ struct vrc_grid {
     // query scratch (grown on demand)
     int* q_cell;           // [cap]
     int* q_rank;           // [cap]
-    int* q_perm;           // [cap]
+    float4* q_pts;         // [cap] the query points in cell order, .w = the query's index
     int* q_count;          // [G^3 + 1]
     int* scan_tmp;         // block sums
     int q_cap;
