@@ -360,7 +360,7 @@ int vrc_levels_from_radius(const float* d_logr, int32_t n, float cell_over_radiu
 /* --------------------------------------------------------------- learned radius
  * Not in the paper: a small network predicts a record's log validity radius from a cheap
  * coarse ray set, so full records are computed only where they are needed; the full
- * record remains the judge (its radius decides coverage).
+ * record decides (its radius sets coverage).
  *
  * vrc_coarse_features: for each position d_pos[i], the coarse stratified ray set of
  * `params` (n_bands x n_bins, jitter seed, rec_base; pole rays excluded) gives
