@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
         float acc_s = 0.f, cmp_s = 0.f, acc_m = 0.f, cmp_m = 0.f;     // lane-owned cell sums
         float mc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mcc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int kmax_rec = 0;
-        int lit_cells = 0, far_evals = 0;                    // lane 0 of each warp counts its warp's cells
+        int lit_cells = 0, far_evals = 0;                    // each lane counts its own cells
         const int CB = a.chunk_bands < nb ? a.chunk_bands : nb;
 
         for (int r0 = 0; r0 < nb; r0 += CB) {
@@ -596,13 +596,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         }
                         m = cell_eval(rr, tt, Lo, sigma_t, g, a.wo, a.ff_signed, v);
                     }
-                    if (a.out.n_cells) {
-                        unsigned lit = __ballot_sync(0xffffffffu, m > 0);
-                        int fsum = m;
-#pragma unroll
-                        for (int o = 16; o >= 1; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
-                        if (lane == 0) { lit_cells += __popc(lit); far_evals += fsum; }
-                    }
+                    lit_cells += m > 0 ? 1 : 0;
+                    far_evals += m;
                     float mine = warp_transpose_reduce(v, lane);
                     if (k == 0) neumaier(acc_s, cmp_s, mine);
                     else neumaier(acc_m, cmp_m, mine);
@@ -886,7 +881,17 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
         }
         if (tid == 0) { misc[1] = 0; misc[3] = 0; }
         __syncthreads();
-        if (lane == 0 && a.out.n_cells) { atomicAdd(&misc[1], lit_cells); atomicAdd(&misc[3], far_evals); }
+        if (a.out.n_cells) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                lit_cells += __shfl_xor_sync(0xffffffffu, lit_cells, o);
+                far_evals += __shfl_xor_sync(0xffffffffu, far_evals, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&misc[1], lit_cells);
+                atomicAdd(&misc[3], far_evals);
+            }
+        }
         __syncthreads();
         const float wms = sc.sigma_s * a.dt;                 // 1 / pdf of a medium shell
         if (warp == 0) {
