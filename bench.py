@@ -116,8 +116,8 @@ def measured_peaks():
 
 
 # DRAM bytes per record of k_records (the pre-pass rays it loads dominate), from one ncu
-# capture of a 1,024-record launch of the mid workload: (65.74 MB + 3.06 MB) / 1,024
-K_RECORDS_DRAM_BYTES_PER_RECORD = (65.739264e6 + 3.059712e6) / 1024
+# capture of a 1,024-record launch of the mid workload: (65.71 MB + 3.17 MB) / 1,024
+K_RECORDS_DRAM_BYTES_PER_RECORD = (65.7088e6 + 3.168768e6) / 1024
 
 
 def fp32_peak_tflops(sm_mhz: float = 2070.0) -> float:
