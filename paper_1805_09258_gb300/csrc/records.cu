@@ -382,10 +382,11 @@ __device__ __noinline__ void write_ellipsoid(const double h[6], const double lam
 }
 
 // ----------------------------------------------------------------- the kernel
-// Registers are capped at 85 per thread: 3 blocks of 256 per SM (24 warps), with the band
-// chunk sized so three blocks' shared memory fits too.  The cell arithmetic spills a little
-// at this cap, but the extra warps hide the latency of the rest: measured 7 % faster on the
-// mid workload and 11 % on the render one than 2 blocks at 128 registers.
+// Registers are capped at 85 per thread: 24 warps per SM, as 3 blocks of 256 (band chunks
+// sized so three blocks' shared memory fits) or 2 blocks of 384 (a whole ray set that fits
+// two blocks).  The cell arithmetic spills a little at this cap, but the extra warps hide the
+// latency of the rest: measured 7 % faster on the mid workload and 11 % on the render one
+// than 2 blocks of 256 at 128 registers.
 #ifndef VRC_RECORDS_REGS
 #define VRC_RECORDS_REGS 85
 #endif
