@@ -158,8 +158,10 @@ def test_hit_ids_agree_except_near_edges(vrc):
 
 def test_light_buffer_shadow_rays_match_bvh_shadow_rays(vrc):
     """Shadow rays through the light buffer test the same triangles with the same predicate
-    as BVH any-hit traversal: records must agree (to float summation order)."""
-    for w, n in ((W.config1(), 64), (W.config2(), 256)):
+    as BVH any-hit traversal, and its per-cell shortcuts (nearer than every candidate: lit;
+    behind a triangle covering the cell: shadowed) give the same answers: records must agree
+    (to float summation order), also on the tessellated 250k-triangle scene."""
+    for w, n in ((W.config1(), 64), (W.config2(), 256), (W.config5(), 64)):
         pos = w.positions(n)
         a = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(shadow_bvh=0))
         b = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(shadow_bvh=1))
