@@ -33,7 +33,8 @@ SLOTS = dict(L=(0, 3), L_ss=(3, 3), L_ms=(6, 3), grad=(9, 9), grad_ss=(18, 9), g
              eig=(94, 3), kappa=(97, 1), status=(98, 1), n_shells=(99, 1), margin_edge=(100, 1),
              margin_t=(101, 1), n_rays=(102, 1), n_degen=(103, 1), L_ff_ss=(104, 3),
              L_ff_ms=(107, 3), L_Y=(110, 1), lam_max=(111, 1), bud_L=(112, 3), bud_L_ff=(115, 3),
-             bud_grad=(118, 3), bud_hess=(121, 3), n_prim_unc=(124, 1), n_unc=(125, 1))
+             bud_grad=(118, 3), bud_hess=(121, 3), n_prim_unc=(124, 1), n_unc=(125, 1), n_replayed=(126, 1),
+             n_bad_replay=(127, 1))
 
 
 def build(force: bool = False) -> str:
@@ -73,7 +74,7 @@ def lib():
         _lib.orc_scene_create.restype = P
         _lib.orc_scene_create.argtypes = [P]
         _lib.orc_scene_destroy.argtypes = [P]
-        _lib.orc_records.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, P, P, P, P, C.c_int]
+        _lib.orc_records.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, P, P, P, P, C.c_int, P, C.c_int]
         _lib.orc_frozen_eval.argtypes = [P, P, P, C.c_int64, P, C.c_int, C.c_int, P]
         _lib.orc_hg.restype = C.c_double
         _lib.orc_hg.argtypes = [C.c_double, C.c_double]
@@ -164,10 +165,18 @@ def make_params(rp, general_derivs: int = 1, track_margins: int = 0, surface_onl
 
 def records(oscene: OracleScene, rp, pos, rec_ids=None, n_bands=None, n_threads: int = 0,
             debug: bool = False, general_derivs: int = 1, track_margins: int = 0,
-            surface_only: int = 0) -> dict:
-    """Compute records at positions `pos` [n,3] (float32).  Returns named float64 arrays."""
+            surface_only: int = 0, replay_hits=None) -> dict:
+    """Compute records at positions `pos` [n,3] (float32).  Returns named float64 arrays.
+
+    replay_hits (optional, int [n, >= rays]): a primary hit primitive id per ray (ray order,
+    the two pole rays last, -1 = no hit) that the oracle uses instead of its own closest
+    hit; the record is then computed in FP64 on those hits, and no primary-ray decision
+    enters the decision budgets (`n_replayed` counts the rays whose id differed)."""
     pos = _f32(pos).reshape(-1, 3)
     n = pos.shape[0]
+    rh = None
+    if replay_hits is not None:
+        rh = np.ascontiguousarray(replay_hits, dtype=np.int32).reshape(n, -1)
     ids = None if rec_ids is None else np.ascontiguousarray(rec_ids, dtype=np.int64)
     nb = None if n_bands is None else np.ascontiguousarray(n_bands, dtype=np.int32)
     out = np.zeros((n, OUT_STRIDE), np.float64)
@@ -181,10 +190,11 @@ def records(oscene: OracleScene, rp, pos, rec_ids=None, n_bands=None, n_threads:
         dh = np.full((n, stride), -2, np.int32)
         dt, dm, dtie = (np.zeros((n, stride)) for _ in range(3))
     lib().orc_records(oscene.ptr, C.byref(p), _p(pos), _p(ids), _p(nb), n, _p(out), n_threads,
-                      _p(dh), _p(dt), _p(dm), _p(dtie), stride)
+                      _p(dh), _p(dt), _p(dm), _p(dtie), stride, _p(rh), 0 if rh is None else rh.shape[1])
     res = {k: out[:, a:a + w] if w > 1 else out[:, a] for k, (a, w) in SLOTS.items()}
     res["status"] = res["status"].astype(np.int32)
     res["n_shells"] = res["n_shells"].astype(np.int32)
+    res["n_replayed"] = res["n_replayed"].astype(np.int32)
     if debug:
         res.update(hit_prim=dh, hit_t=dt, hit_margin=dm, hit_tie=dtie)
     return res

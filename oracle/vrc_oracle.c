@@ -75,7 +75,9 @@ enum {
     O_LFF_MS = 107, O_LY = 110, O_LAMMAX = 111,
     /* decision-sensitivity budgets (filled when track_margins = 1): the largest change
      * that flipping every near-tie decision of the record could make */
-    O_BUD_L = 112, O_BUD_LFF = 115, O_BUD_G = 118, O_BUD_H = 121, O_N_PRIM_UNC = 124, O_N_UNC = 125
+    O_BUD_L = 112, O_BUD_LFF = 115, O_BUD_G = 118, O_BUD_H = 121, O_N_PRIM_UNC = 124, O_N_UNC = 125,
+    /* replay mode: rays whose given primary hit differs from the oracle's own, ids out of range */
+    O_N_REPLAYED = 126, O_N_BAD_REPLAY = 127
 };
 
 /* a discrete decision is "near-tie" when FP32 rounding could flip it */
@@ -491,7 +493,12 @@ double orc_hg(double mu, double g) {
 }
 
 /* ---------------------------------------------------- vertex radiance (R11) */
-static void surface_radiance(const orc_scene* s, int id, v3 y, v3 d, double Lo[3], double dLo[3], int track) {
+/* Vertex radiance with its shadow-ray decisions.  When track is set, every light whose
+ * shadow ray passes within TIE_EDGE of a triangle edge (a decision FP32 may take the
+ * other way) adds |its term| to dLo, its signed change if the ray went the other way
+ * to sLo, and 1 to *nsh.  dLo, sLo and nsh may be NULL when track is 0. */
+static void surface_radiance(const orc_scene* s, int id, v3 y, v3 d, double Lo[3], double dLo[3], double sLo[3],
+                             int* nsh, int track) {
     const orc_scene_in* in = &s->in;
     Lo[0] = Lo[1] = Lo[2] = 0.0;
     if (in->emission)
@@ -513,15 +520,18 @@ static void surface_radiance(const orc_scene* s, int id, v3 y, v3 d, double Lo[3
         double margin = INFINITY;
         int occ = occluded(s, o, scl(lo, 1.0 / dl), dl, &margin, track);
         double T = exp(-s->sigma_t * dist);
+        int near = track && margin < TIE_EDGE;
         for (int c = 0; c < 3; ++c) {
             double v = (double)in->albedo[3 * id + c] / ORC_PI * (double)in->light_I[3 * L + c] * cs * T / (dist * dist);
             if (!occ) Lo[c] += v;
-            if (margin < TIE_EDGE) dLo[c] += fabs(v);
+            if (near) { dLo[c] += fabs(v); sLo[c] += occ ? v : -v; }
         }
+        if (near) ++*nsh;
     }
 }
 
-static void medium_radiance(const orc_scene* s, v3 y, v3 d, double Lo[3], double dLo[3], int track) {
+static void medium_radiance(const orc_scene* s, v3 y, v3 d, double Lo[3], double dLo[3], double sLo[3], int* nsh,
+                            int track) {
     const orc_scene_in* in = &s->in;
     Lo[0] = Lo[1] = Lo[2] = 0.0;
     for (int L = 0; L < in->n_lights; ++L) {
@@ -535,11 +545,13 @@ static void medium_radiance(const orc_scene* s, v3 y, v3 d, double Lo[3], double
         double mu = dot(lh, d);
         double f = orc_hg(mu, (double)in->g);
         double T = exp(-s->sigma_t * dist);
+        int near = track && margin < TIE_EDGE;
         for (int c = 0; c < 3; ++c) {
             double v = f * (double)in->light_I[3 * L + c] * T / (dist * dist);
             if (!occ) Lo[c] += v;
-            if (dLo && margin < TIE_EDGE) dLo[c] += fabs(v);
+            if (near) { dLo[c] += fabs(v); sLo[c] += occ ? v : -v; }
         }
+        if (near) ++*nsh;
     }
 }
 
@@ -844,19 +856,28 @@ int orc_aniso(double LY, const double* h6, double eps, double r_min, double r_ma
 /* ---------------------------------------------------- one record (Secs. 4-5) */
 typedef struct {
     int nb, ns, V, N, K;
+    int replay;        /* 1: primary hits were given (no primary decision is uncertain) */
     v3 x;
     v3* dir;
     double* t_end;
     int* hit;
     double* Lo_surf;   /* [V][3] */
     double* Lo_med;    /* [K][V][3] */
-    double* dLo_surf;  /* [V][3]    near-tie uncertainty of each vertex radiance */
+    /* shadow-ray decisions near a tie: |change| summed over lights, signed change, count */
+    double* dLo_surf;  /* [V][3] */
+    double* sLo_surf;  /* [V][3] */
+    int* nsh_surf;     /* [V] */
     double* dLo_med;   /* [K][V][3] */
-    unsigned char* unc_clamp;   /* [K][V] clamp decision near a tie */
+    double* sLo_med;   /* [K][V][3] */
+    int* nsh_med;      /* [K][V] */
+    unsigned char* unc_clamp;   /* [K][V] clamp decision (t_k against the ray's end) near a tie */
+    double* calt_Lo_med;        /* [K][V][3] radiance of the unclamped alternative of a clamped vertex */
     unsigned char* unc_prim;    /* [V] primary hit near a tie */
     double* margin_e;  /* per primary ray: edge margin */
     double* tie;
     double* t_unc;     /* [V] relative uncertainty of t_end: TIE_T (1 + 1/|cos incidence|) */
+    int n_replayed;    /* rays whose given hit differs from the oracle's own */
+    int n_bad_replay;  /* given hit ids out of range (ignored) */
     /* the other outcome of a near-tie primary ray (found by re-tracing perturbed directions) */
     double* alt_t;     /* [V] */
     int* alt_hit;      /* [V] */
@@ -866,21 +887,39 @@ typedef struct {
 
 static void shells_free(shells_t* S) {
     free(S->dir); free(S->t_end); free(S->hit); free(S->Lo_surf); free(S->Lo_med);
-    free(S->dLo_surf); free(S->dLo_med); free(S->unc_clamp); free(S->unc_prim);
+    free(S->dLo_surf); free(S->sLo_surf); free(S->nsh_surf);
+    free(S->dLo_med); free(S->sLo_med); free(S->nsh_med);
+    free(S->unc_clamp); free(S->calt_Lo_med); free(S->unc_prim);
     free(S->margin_e); free(S->tie); free(S->t_unc);
     free(S->alt_t); free(S->alt_hit); free(S->alt_Lo_surf); free(S->alt_Lo_med);
 }
 
-/* trace the ray set, the shells and every vertex radiance (Sec. 4, Sec. 6 Implementation) */
-static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, int ns, int64_t rec, shells_t* S) {
+/* plane parameter of the ray (x, d) on triangle id, ignoring its edges (replayed hits) */
+static int plane_t(const orc_scene* s, int id, v3 x, v3 d, double* t) {
+    otri T;
+    T.a = ldv(s->in.tri_v + 9 * id);
+    T.b = ldv(s->in.tri_v + 9 * id + 3);
+    T.c = ldv(s->in.tri_v + 9 * id + 6);
+    double u, v;
+    return mt(x, d, &T, t, &u, &v) && *t > 0.0;
+}
+
+/* trace the ray set, the shells and every vertex radiance (Sec. 4, Sec. 6 Implementation).
+ * replay (nullable): a primary hit id per ray (-1 = no hit) to use instead of the oracle's
+ * own closest hit (reading R16's replay: the reduction is then compared on the same hits). */
+static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, int ns, int64_t rec,
+                         const int32_t* replay, shells_t* S) {
     memset(S, 0, sizeof(*S));
     S->nb = nb; S->ns = ns; S->N = nb * ns; S->V = S->N + 2; S->x = x;
+    S->replay = replay != NULL;
     int V = S->V, track = p->track_margins;
     S->dir = (v3*)malloc(sizeof(v3) * V);
     S->t_end = (double*)malloc(sizeof(double) * V);
     S->hit = (int*)malloc(sizeof(int) * V);
     S->Lo_surf = (double*)calloc((size_t)V * 3, sizeof(double));
     S->dLo_surf = (double*)calloc((size_t)V * 3, sizeof(double));
+    S->sLo_surf = (double*)calloc((size_t)V * 3, sizeof(double));
+    S->nsh_surf = (int*)calloc((size_t)V, sizeof(int));
     S->unc_prim = (unsigned char*)calloc((size_t)V, 1);
     S->margin_e = (double*)malloc(sizeof(double) * V);
     S->tie = (double*)malloc(sizeof(double) * V);
@@ -905,13 +944,23 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
             double tie_val = INFINITY;
             id = closest_hit(s, x, d, &t, &S->margin_e[v], &S->tie[v], &tie_val, track);
             if (track && (S->margin_e[v] < TIE_EDGE || tie_val < TIE_T)) S->unc_prim[v] = 1;
+            if (replay) {
+                int rid = replay[v];
+                double tr;
+                if (rid < -1 || rid >= s->n || (rid >= 0 && !plane_t(s, rid, x, d, &tr))) {
+                    S->n_bad_replay++;                 /* keep the oracle's own hit */
+                } else if (rid != id) {
+                    S->n_replayed++;
+                    id = rid;
+                    if (rid >= 0) t = tr;
+                }
+                S->unc_prim[v] = 0;                    /* the decision is the given one */
+            }
         }
         double cinc = 1.0;                           /* |cos| between the ray and the surface it ends on */
         if (id >= 0 && !s->in.sphere_mode) {
-            const otri* T = NULL;
             v3 a = ldv(s->in.tri_v + 9 * id), b = ldv(s->in.tri_v + 9 * id + 3), c = ldv(s->in.tri_v + 9 * id + 6);
             v3 n = cross(sub(b, a), sub(c, a));
-            (void)T;
             cinc = fabs(dot(n, d)) / norm(n);
         } else if (id < 0) {
             cinc = fmax(fabs(d.x), fmax(fabs(d.y), fabs(d.z)));  /* lower bound over the exit face */
@@ -930,7 +979,8 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
             if (s->in.sphere_mode) {
                 for (int c = 0; c < 3; ++c) S->Lo_surf[3 * v + c] = (double)s->in.sphere_Le[c];
             } else {
-                surface_radiance(s, id, y, d, &S->Lo_surf[3 * v], &S->dLo_surf[3 * v], track);
+                surface_radiance(s, id, y, d, &S->Lo_surf[3 * v], &S->dLo_surf[3 * v], &S->sLo_surf[3 * v],
+                                 &S->nsh_surf[v], track);
             }
         } else {
             S->t_end[v] = cube_exit(x, d);
@@ -958,10 +1008,9 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
                     S->alt_hit[v] = iq;
                 }
             }
-            if (S->alt_hit[v] >= 0 && S->alt_hit[v] != S->hit[v]) {
-                double dummy[3] = {0, 0, 0};
-                surface_radiance(s, S->alt_hit[v], add(x, scl(d, S->alt_t[v])), d, &S->alt_Lo_surf[3 * v], dummy, 0);
-            }
+            if (S->alt_hit[v] >= 0 && S->alt_hit[v] != S->hit[v])
+                surface_radiance(s, S->alt_hit[v], add(x, scl(d, S->alt_t[v])), d, &S->alt_Lo_surf[3 * v], NULL, NULL,
+                                 NULL, 0);
             if (S->alt_t[v] > tmax) tmax = S->alt_t[v];
         }
         if (S->t_end[v] > tmax) tmax = S->t_end[v];
@@ -971,7 +1020,10 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
     size_t KV = (size_t)(S->K > 0 ? S->K : 1) * V;
     S->Lo_med = (double*)calloc(KV * 3, sizeof(double));
     S->dLo_med = (double*)calloc(KV * 3, sizeof(double));
+    S->sLo_med = (double*)calloc(KV * 3, sizeof(double));
+    S->nsh_med = (int*)calloc(KV, sizeof(int));
     S->unc_clamp = (unsigned char*)calloc(KV, 1);
+    S->calt_Lo_med = (double*)calloc(KV * 3, sizeof(double));
     S->alt_Lo_med = (double*)calloc(KV * 3, sizeof(double));
     for (int k = 1; k <= S->K; ++k) {
         double tk = ((double)k - 0.5) * dt;
@@ -979,44 +1031,107 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
             size_t o = (size_t)(k - 1) * V + v;
             v3 y = add(x, scl(S->dir[v], tk));
             int near = track && fabs(tk - S->t_end[v]) < S->t_unc[v] * S->t_end[v];
-            if (tk < S->t_end[v]) {
-                medium_radiance(s, y, S->dir[v], &S->Lo_med[3 * o], &S->dLo_med[3 * o], track);
-                if (near)
-                    for (int c = 0; c < 3; ++c) S->dLo_med[3 * o + c] += fabs(S->Lo_med[3 * o + c]);
-            } else if (near) {
-                /* clamped now; the alternative is an unclamped medium vertex at t_k */
-                double alt[3];
-                medium_radiance(s, y, S->dir[v], alt, NULL, 0);
-                for (int c = 0; c < 3; ++c) S->dLo_med[3 * o + c] += fabs(alt[c]);
-            }
+            if (tk < S->t_end[v])
+                medium_radiance(s, y, S->dir[v], &S->Lo_med[3 * o], &S->dLo_med[3 * o], &S->sLo_med[3 * o],
+                                &S->nsh_med[o], track);
+            else if (near)      /* clamped now; the alternative is an unclamped medium vertex at t_k */
+                medium_radiance(s, y, S->dir[v], &S->calt_Lo_med[3 * o], NULL, NULL, NULL, 0);
             if (near) S->unc_clamp[o] = 1;
             if (S->unc_prim[v] && tk < S->alt_t[v]) {
                 if (tk < S->t_end[v]) memcpy(&S->alt_Lo_med[3 * o], &S->Lo_med[3 * o], 3 * sizeof(double));
-                else medium_radiance(s, y, S->dir[v], &S->alt_Lo_med[3 * o], NULL, 0);
+                else medium_radiance(s, y, S->dir[v], &S->alt_Lo_med[3 * o], NULL, NULL, NULL, 0);
             }
         }
     }
 }
 
-/* vertex v of shell k (k = 0 surface shell, k >= 1 medium shell): ray parameter,
- * radiance, near-tie uncertainty of that radiance, and whether its clamp is near a tie */
-static double vertex_t(const shells_t* S, const orc_params* p, int k, int v, const double** Lo, const double** dLo,
-                       int* unc) {
-    static const double zero[3] = {0, 0, 0};
+/* The discrete decisions of one vertex that FP32 may take the other way: its primary ray's
+ * hit (ALT_PRIM), its clamp at the ray's end (ALT_CLAMP, medium shells), its shadow ray
+ * (ALT_SHADOW, one light near a tie). */
+enum { ALT_SHADOW = 1, ALT_CLAMP = 2, ALT_PRIM = 4 };
+
+/* vertex v of shell k (k = 0 surface shell, k >= 1 medium shell) with the decisions in
+ * `alts` taken the other way: its ray parameter (returned), radiance, the relative
+ * uncertainty of that parameter's comparison with other vertices', and *open = 1 for an
+ * unclamped medium vertex (every such vertex of a shell sits at the same t_k, in any
+ * precision, and a clamped one at its ray's end t_end <= t_k) */
+static double vertex_state(const shells_t* S, const orc_params* p, int k, int v, int alts, double Lo[3],
+                           double* t_tol, int* open) {
+    Lo[0] = Lo[1] = Lo[2] = 0.0;
+    *t_tol = S->t_unc[v] + 2.0 * TIE_T;
+    *open = 0;
     if (k == 0) {
-        *Lo = S->hit[v] >= 0 ? &S->Lo_surf[3 * v] : zero;
-        *dLo = &S->dLo_surf[3 * v];
-        *unc = 0;
+        if (alts & ALT_PRIM) {
+            if (S->alt_hit[v] >= 0) memcpy(Lo, &S->alt_Lo_surf[3 * v], 3 * sizeof(double));
+            return S->alt_t[v];
+        }
+        if (S->hit[v] >= 0) {
+            memcpy(Lo, &S->Lo_surf[3 * v], 3 * sizeof(double));
+            if (alts & ALT_SHADOW)
+                for (int c = 0; c < 3; ++c) Lo[c] += S->sLo_surf[3 * v + c];
+        }
         return S->t_end[v];
     }
     size_t o = (size_t)(k - 1) * S->V + v;
-    *dLo = &S->dLo_med[3 * o];
-    *unc = S->unc_clamp[o];
+    double tk = ((double)k - 0.5) * (double)p->dt;
+    if (alts & ALT_PRIM) {
+        if (tk < S->alt_t[v]) {
+            memcpy(Lo, &S->alt_Lo_med[3 * o], 3 * sizeof(double));
+            *t_tol = 2.0 * TIE_T;
+            *open = 1;
+            return tk;
+        }
+        return S->alt_t[v];
+    }
+    int unclamped = tk < S->t_end[v];
+    if (alts & ALT_CLAMP) {
+        if (unclamped) return tk;                    /* clamped instead: zero-radiance sample at t_end <= t_k */
+        memcpy(Lo, &S->calt_Lo_med[3 * o], 3 * sizeof(double));
+        *t_tol = 2.0 * TIE_T;
+        *open = 1;
+        return tk;
+    }
+    if (!unclamped) return S->t_end[v];              /* zero-radiance sample at the occluder (Sec. 4) */
+    memcpy(Lo, &S->Lo_med[3 * o], 3 * sizeof(double));
+    if (alts & ALT_SHADOW)
+        for (int c = 0; c < 3; ++c) Lo[c] += S->sLo_med[3 * o + c];
+    *t_tol = 2.0 * TIE_T;
+    *open = 1;
+    return tk;
+}
+
+/* a furthest-vertex set that rounding can produce: nonempty, within the near-furthest
+ * vertices, and holding every open vertex of a medium-shell cell (they share t_k, and a
+ * clamped vertex never lies beyond it) */
+static int far_set_valid(int fs, int nearm, int openm) {
+    if (fs == 0 || (fs & nearm) != fs) return 0;
+    return (fs & openm) == openm;
+}
+
+static int far_set_ambiguous(int nearm, int openm) {
+    if (openm) return (nearm & ~openm) != 0;
+    return (nearm & (nearm - 1)) != 0;               /* two or more near-furthest vertices */
+}
+
+/* vertex v of shell k as computed: ray parameter and radiance */
+static double vertex_t(const shells_t* S, const orc_params* p, int k, int v, const double** Lo) {
+    static const double zero[3] = {0, 0, 0};
+    if (k == 0) {
+        *Lo = S->hit[v] >= 0 ? &S->Lo_surf[3 * v] : zero;
+        return S->t_end[v];
+    }
+    size_t o = (size_t)(k - 1) * S->V + v;
     double tk = ((double)k - 0.5) * (double)p->dt;
     if (tk < S->t_end[v]) { *Lo = &S->Lo_med[3 * o]; return tk; }
     *Lo = zero;                                      /* zero-radiance sample at the occluder (Sec. 4) */
     return S->t_end[v];
 }
+
+/* the change one decision makes to the record, summed (as vectors) over the cells it touches */
+typedef struct {
+    int kind, k, v;
+    double L[3], g[3][3], H[3][3][3];
+} decision_t;
 
 typedef struct {
     double L[3], g[3][3], H[3][3][3];
@@ -1024,7 +1139,189 @@ typedef struct {
     int n_degen;
     double bud_L[3], bud_g[3], bud_H[3];
     int n_unc;
+    decision_t* dec;   /* decisions whose cells each hold no other uncertain decision */
+    int n_dec, cap_dec;
 } ffsum;
+
+static decision_t* find_decision(ffsum* acc, int kind, int k, int v) {
+    for (int i = 0; i < acc->n_dec; ++i)
+        if (acc->dec[i].kind == kind && acc->dec[i].k == k && acc->dec[i].v == v) return &acc->dec[i];
+    if (acc->n_dec == acc->cap_dec) {
+        acc->cap_dec = acc->cap_dec ? 2 * acc->cap_dec : 16;
+        acc->dec = (decision_t*)realloc(acc->dec, sizeof(decision_t) * (size_t)acc->cap_dec);
+    }
+    decision_t* d = &acc->dec[acc->n_dec++];
+    memset(d, 0, sizeof(*d));
+    d->kind = kind; d->k = k; d->v = v;
+    return d;
+}
+
+/* One cell of shell k with the decisions alts[q] of its vertices taken the other way.
+ * far_set (bit mask) overrides the furthest vertices when nonzero.  Fills *co (zero for a
+ * dark or degenerate cell) and *near_set: the vertices whose parameter is within FP32
+ * rounding of the largest, any nonempty subset of which FP32 may take as the furthest. */
+static int eval_cell(const orc_scene* s, const shells_t* S, const orc_params* p, v3 x_eval, int k, const int vi[3],
+                     const int alts[3], int far_set, double weight, cellout* co, int* near_set, int* open_set) {
+    double Lo[3][3], t[3], tol[3];
+    int op[3];
+    v3 y[3];
+    for (int q = 0; q < 3; ++q) {
+        t[q] = vertex_state(S, p, k, vi[q], alts[q], Lo[q], &tol[q], &op[q]);
+        y[q] = add(S->x, scl(S->dir[vi[q]], t[q]));
+    }
+    double tmx = fmax(t[0], fmax(t[1], t[2]));
+    int canon = 0, nearm = 0, openm = 0;
+    for (int q = 0; q < 3; ++q) {
+        if (t[q] == tmx) canon |= 1 << q;
+        if (tmx - t[q] <= tol[q] * tmx) nearm |= 1 << q;
+        if (op[q]) openm |= 1 << q;
+    }
+    if (near_set) *near_set = nearm;
+    if (open_set) *open_set = openm;
+    int fs = far_set ? far_set : canon;
+    v3 yf[3];
+    const double* Lf[3];
+    int nf = 0, dark = 1;
+    for (int q = 0; q < 3; ++q)
+        if (fs & (1 << q)) {
+            yf[nf] = y[q]; Lf[nf] = Lo[q]; ++nf;
+            if (Lo[q][0] != 0.0 || Lo[q][1] != 0.0 || Lo[q][2] != 0.0) dark = 0;
+        }
+    memset(co, 0, sizeof(*co));
+    if (dark) return 1;
+    v3 wo = ldv(p->omega_o);
+    int ok = cell_radiance(x_eval, y[0], y[1], y[2], nf, yf, Lf, s->sigma_t, (double)s->in.g, wo, weight,
+                           p->general_derivs, p->ff_signed, co);
+    if (!ok) memset(co, 0, sizeof(*co));
+    return ok;
+}
+
+static void cell_diff_norms(const cellout* a, const cellout* b, double nL[3], double ng[3], double nH[3]) {
+    for (int ch = 0; ch < 3; ++ch) {
+        double gn = 0, hn = 0;
+        for (int i = 0; i < 3; ++i) {
+            double dg = a->g[ch][i] - b->g[ch][i];
+            gn += dg * dg;
+            for (int j = 0; j < 3; ++j) {
+                double dh = a->H[ch][i][j] - b->H[ch][i][j];
+                hn += dh * dh;
+            }
+        }
+        nL[ch] = fabs(a->L[ch] - b->L[ch]);
+        ng[ch] = sqrt(gn);
+        nH[ch] = sqrt(hn);
+    }
+}
+
+/* Decision budget of one cell (track_margins).  The record's change under any set of
+ * flipped decisions is the sum over cells of each cell's change.  A cell touched by exactly
+ * one binary decision, with an unambiguous furthest-vertex set both ways, changes by that
+ * decision's exact difference: it is added (as a vector) to the decision's total, whose
+ * norm enters the budget once.  Any other cell (several decisions, an ambiguous furthest
+ * set, several lights near a tie at one vertex) adds the largest change over every
+ * combination of its decisions and furthest sets.  The budget therefore bounds the change
+ * of every combination, and equals it when a single decision flips. */
+static void cell_budget(const orc_scene* s, const shells_t* S, const orc_params* p, v3 x_eval, int k, int c,
+                        const int vi[3], double weight, ffsum* acc) {
+    int dq[12], dk[12];
+    int nd = 0, multi = 0;
+    for (int q = 0; q < 3; ++q) {
+        int v = vi[q];
+        if (!S->replay && S->unc_prim[v]) { dq[nd] = q; dk[nd] = ALT_PRIM; ++nd; }
+        int nsh;
+        if (k == 0) nsh = S->hit[v] >= 0 ? S->nsh_surf[v] : 0;
+        else {
+            size_t o = (size_t)(k - 1) * S->V + v;
+            double tk = ((double)k - 0.5) * (double)p->dt;
+            nsh = tk < S->t_end[v] ? S->nsh_med[o] : 0;
+            if (S->unc_clamp[o]) { dq[nd] = q; dk[nd] = ALT_CLAMP; ++nd; }
+        }
+        if (nsh == 1) { dq[nd] = q; dk[nd] = ALT_SHADOW; ++nd; }
+        else if (nsh > 1) multi = 1;
+    }
+    static const int none[3] = {0, 0, 0};
+    cellout cur;
+    int near_cur, open_cur;
+    eval_cell(s, S, p, x_eval, k, vi, none, 0, weight, &cur, &near_cur, &open_cur);
+    int amb_cur = far_set_ambiguous(near_cur, open_cur);
+    if (nd == 0 && !amb_cur && !multi) return;
+    acc->n_unc++;
+    if (nd == 1 && !amb_cur && !multi) {
+        int alts[3] = {0, 0, 0};
+        alts[dq[0]] = dk[0];
+        cellout alt;
+        int near_alt, open_alt;
+        eval_cell(s, S, p, x_eval, k, vi, alts, 0, weight, &alt, &near_alt, &open_alt);
+        if (!far_set_ambiguous(near_alt, open_alt)) {
+            decision_t* d = find_decision(acc, dk[0], dk[0] == ALT_PRIM ? -1 : k, vi[dq[0]]);
+            for (int ch = 0; ch < 3; ++ch) {
+                d->L[ch] += alt.L[ch] - cur.L[ch];
+                for (int i = 0; i < 3; ++i) {
+                    d->g[ch][i] += alt.g[ch][i] - cur.g[ch][i];
+                    for (int j = 0; j < 3; ++j) d->H[ch][i][j] += alt.H[ch][i][j] - cur.H[ch][i][j];
+                }
+            }
+            return;
+        }
+    }
+    /* every combination of the cell's decisions and of its furthest sets */
+    double mL[3] = {0, 0, 0}, mg[3] = {0, 0, 0}, mH[3] = {0, 0, 0};
+    for (int combo = 0; combo < (1 << nd); ++combo) {
+        int alts[3] = {0, 0, 0};
+        for (int i = 0; i < nd; ++i)
+            if (combo & (1 << i)) alts[dq[i]] |= dk[i];
+        int nearm, openm;
+        cellout co;
+        eval_cell(s, S, p, x_eval, k, vi, alts, 0, weight, &co, &nearm, &openm);
+        for (int fs = 1; fs < 8; ++fs) {           /* every furthest set rounding can produce */
+            if (!far_set_valid(fs, nearm, openm)) continue;
+            eval_cell(s, S, p, x_eval, k, vi, alts, fs, weight, &co, NULL, NULL);
+            double nL[3], ng[3], nH[3];
+            cell_diff_norms(&co, &cur, nL, ng, nH);
+            for (int ch = 0; ch < 3; ++ch) {
+                mL[ch] = fmax(mL[ch], nL[ch]);
+                mg[ch] = fmax(mg[ch], ng[ch]);
+                mH[ch] = fmax(mH[ch], nH[ch]);
+            }
+        }
+    }
+    if (multi) {
+        /* several lights near a tie at one vertex: bound the change of its radiance by the
+         * sum of those lights' terms, carried by the furthest vertex */
+        double U[3] = {0, 0, 0};
+        for (int q = 0; q < 3; ++q) {
+            const double* dl;
+            if (k == 0) dl = &S->dLo_surf[3 * vi[q]];
+            else dl = &S->dLo_med[3 * ((size_t)(k - 1) * S->V + vi[q])];
+            for (int ch = 0; ch < 3; ++ch) U[ch] += dl[ch];
+        }
+        double Lo_dummy[3], tol, tq[3];
+        int opq;
+        v3 y[3];
+        for (int q = 0; q < 3; ++q) {
+            tq[q] = vertex_state(S, p, k, vi[q], 0, Lo_dummy, &tol, &opq);
+            y[q] = add(S->x, scl(S->dir[vi[q]], tq[q]));
+        }
+        int qf = tq[0] >= tq[1] && tq[0] >= tq[2] ? 0 : (tq[1] >= tq[2] ? 1 : 2);
+        v3 yf = y[qf];
+        const double* Up[1] = {U};
+        cellout cu;
+        v3 wo = ldv(p->omega_o);
+        if (cell_radiance(x_eval, y[0], y[1], y[2], 1, &yf, Up, s->sigma_t, (double)s->in.g, wo, weight,
+                          p->general_derivs, p->ff_signed, &cu)) {
+            static const cellout zero_cell;
+            double nL[3], ng[3], nH[3];
+            cell_diff_norms(&cu, &zero_cell, nL, ng, nH);
+            for (int ch = 0; ch < 3; ++ch) { mL[ch] += nL[ch]; mg[ch] += ng[ch]; mH[ch] += nH[ch]; }
+        }
+    }
+    (void)c;
+    for (int ch = 0; ch < 3; ++ch) {
+        acc->bud_L[ch] += mL[ch];
+        acc->bud_g[ch] += mg[ch];
+        acc->bud_H[ch] += mH[ch];
+    }
+}
 
 /* Eqs. ApprxRadiance, SegmentRadianceGradient, SegmentRadianceHessian over a range of
  * shells, evaluated at x_eval with the vertices and furthest-vertex choices of S frozen */
@@ -1038,12 +1335,11 @@ static void ff_accumulate(const orc_scene* s, const shells_t* S, const orc_param
         for (int c = 0; c < ncell; ++c) {
             int vi[3];
             cell_vertices(S->nb, S->ns, c, &vi[0], &vi[1], &vi[2]);
-            const double *Lo[3], *dLo[3];
-            int unc[3];
+            const double* Lo[3];
             double t[3];
             v3 y[3];
             for (int q = 0; q < 3; ++q) {
-                t[q] = vertex_t(S, p, k, vi[q], &Lo[q], &dLo[q], &unc[q]);
+                t[q] = vertex_t(S, p, k, vi[q], &Lo[q]);
                 y[q] = add(S->x, scl(S->dir[vi[q]], t[q]));
             }
             /* furthest vertices (R9): all vertices at the largest t */
@@ -1053,83 +1349,7 @@ static void ff_accumulate(const orc_scene* s, const shells_t* S, const orc_param
             const double* Lf[3];
             for (int q = 0; q < 3; ++q)
                 if (t[q] == tmx) { yf[nf] = y[q]; Lf[nf] = Lo[q]; ++nf; }
-            if (p->track_margins) {
-                /* bound on what flipping this cell's near-tie decisions could change:
-                 * any vertex radiance within its uncertainty, and, when the furthest-vertex
-                 * set or a clamp is near a tie, any of the three vertex radiances */
-                int choice_unc = unc[0] | unc[1] | unc[2];
-                if (k == 0)
-                    for (int q = 0; q < 3; ++q)
-                        if (t[q] != tmx && tmx - t[q] < (S->t_unc[vi[q]] + 2.0 * TIE_T) * tmx) choice_unc = 1;
-                double U[3] = {0, 0, 0};
-                for (int q = 0; q < 3; ++q)
-                    for (int ch = 0; ch < 3; ++ch) U[ch] += dLo[q][ch] + (choice_unc ? 2.0 * fabs(Lo[q][ch]) : 0.0);
-                if (U[0] > 0 || U[1] > 0 || U[2] > 0) {
-                    cellout cu;
-                    const double* Up[1] = {U};
-                    if (cell_radiance(x_eval, y[0], y[1], y[2], 1, &yf[0], Up, s->sigma_t, (double)s->in.g, wo, weight,
-                                      p->general_derivs, p->ff_signed, &cu)) {
-                        for (int ch = 0; ch < 3; ++ch) {
-                            double gn = 0, hn = 0;
-                            for (int i = 0; i < 3; ++i) {
-                                gn += cu.g[ch][i] * cu.g[ch][i];
-                                for (int j = 0; j < 3; ++j) hn += cu.H[ch][i][j] * cu.H[ch][i][j];
-                            }
-                            acc->bud_L[ch] += fabs(cu.L[ch]);
-                            acc->bud_g[ch] += sqrt(gn);
-                            acc->bud_H[ch] += sqrt(hn);
-                        }
-                    }
-                    acc->n_unc++;
-                }
-                /* a near-tie primary ray may end elsewhere: add |alternative - current| of this cell */
-                for (int q = 0; q < 3; ++q) {
-                    int v = vi[q];
-                    if (!S->unc_prim[v]) continue;
-                    static const double zero[3] = {0, 0, 0};
-                    double ta[3] = {t[0], t[1], t[2]};
-                    const double* La[3] = {Lo[0], Lo[1], Lo[2]};
-                    v3 ya[3] = {y[0], y[1], y[2]};
-                    if (k == 0) {
-                        ta[q] = S->alt_t[v];
-                        La[q] = S->alt_hit[v] >= 0 ? &S->alt_Lo_surf[3 * v] : zero;
-                    } else {
-                        double tk = ((double)k - 0.5) * (double)p->dt;
-                        size_t o = (size_t)(k - 1) * S->V + v;
-                        ta[q] = tk < S->alt_t[v] ? tk : S->alt_t[v];
-                        La[q] = tk < S->alt_t[v] ? &S->alt_Lo_med[3 * o] : zero;
-                    }
-                    ya[q] = add(S->x, scl(S->dir[v], ta[q]));
-                    double tma = fmax(ta[0], fmax(ta[1], ta[2]));
-                    int na = 0;
-                    v3 yfa[3];
-                    const double* Lfa[3];
-                    for (int r = 0; r < 3; ++r)
-                        if (ta[r] == tma) { yfa[na] = ya[r]; Lfa[na] = La[r]; ++na; }
-                    cellout c0, c1;
-                    int ok0 = cell_radiance(x_eval, y[0], y[1], y[2], nf, yf, Lf, s->sigma_t, (double)s->in.g, wo,
-                                            weight, p->general_derivs, p->ff_signed, &c0);
-                    int ok1 = cell_radiance(x_eval, ya[0], ya[1], ya[2], na, yfa, Lfa, s->sigma_t, (double)s->in.g,
-                                            wo, weight, p->general_derivs, p->ff_signed, &c1);
-                    if (!ok0) memset(&c0, 0, sizeof(c0));
-                    if (!ok1) memset(&c1, 0, sizeof(c1));
-                    for (int ch = 0; ch < 3; ++ch) {
-                        double gn = 0, hn = 0;
-                        for (int i = 0; i < 3; ++i) {
-                            double dg = c1.g[ch][i] - c0.g[ch][i];
-                            gn += dg * dg;
-                            for (int j = 0; j < 3; ++j) {
-                                double dh = c1.H[ch][i][j] - c0.H[ch][i][j];
-                                hn += dh * dh;
-                            }
-                        }
-                        acc->bud_L[ch] += fabs(c1.L[ch] - c0.L[ch]);
-                        acc->bud_g[ch] += sqrt(gn);
-                        acc->bud_H[ch] += sqrt(hn);
-                    }
-                    acc->n_unc++;
-                }
-            }
+            if (p->track_margins) cell_budget(s, S, p, x_eval, k, c, vi, weight, acc);
             int dark = 1;
             for (int q = 0; q < nf; ++q)
                 if (Lf[q][0] != 0.0 || Lf[q][1] != 0.0 || Lf[q][2] != 0.0) dark = 0;
@@ -1153,17 +1373,35 @@ static void ff_accumulate(const orc_scene* s, const shells_t* S, const orc_param
             }
         }
     }
+    /* each decision's total change enters the budget once */
+    for (int i = 0; i < acc->n_dec; ++i) {
+        const decision_t* d = &acc->dec[i];
+        for (int ch = 0; ch < 3; ++ch) {
+            double gn = 0, hn = 0;
+            for (int a = 0; a < 3; ++a) {
+                gn += d->g[ch][a] * d->g[ch][a];
+                for (int b = 0; b < 3; ++b) hn += d->H[ch][a][b] * d->H[ch][a][b];
+            }
+            acc->bud_L[ch] += fabs(d->L[ch]);
+            acc->bud_g[ch] += sqrt(gn);
+            acc->bud_H[ch] += sqrt(hn);
+        }
+    }
+    free(acc->dec);
+    acc->dec = NULL;
+    acc->n_dec = acc->cap_dec = 0;
 }
 
 static void pack_h6(const double H[3][3], double* o) {
     o[0] = H[0][0]; o[1] = H[0][1]; o[2] = H[0][2]; o[3] = H[1][1]; o[4] = H[1][2]; o[5] = H[2][2];
 }
 
-static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb, int ns, int64_t rec, double* out,
-                           int32_t* dbg_hit, double* dbg_t, double* dbg_margin, double* dbg_tie) {
+static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb, int ns, int64_t rec,
+                           const int32_t* replay, double* out, int32_t* dbg_hit, double* dbg_t, double* dbg_margin,
+                           double* dbg_tie) {
     memset(out, 0, sizeof(double) * ORC_OUT_STRIDE);
     shells_t S;
-    build_shells(s, x, p, nb, ns, rec, &S);
+    build_shells(s, x, p, nb, ns, rec, replay, &S);
     /* Monte Carlo radiance (Eqs. outLF, mediaLFin, curveLFin with equal-solid-angle strata) */
     v3 wo = ldv(p->omega_o);
     double dt = (double)p->dt, st = s->sigma_t, ss = (double)s->in.sigma_s;
@@ -1186,6 +1424,10 @@ static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb
             if (tk < S.t_end[v])
                 for (int c = 0; c < 3; ++c) Lms[c] += w * ss * dt * T * S.Lo_med[3 * o + c];
             for (int c = 0; c < 3; ++c) bud[c] += w * ss * dt * T * S.dLo_med[3 * o + c];
+            if (S.unc_clamp[o]) {   /* the clamp taken the other way adds or removes this vertex's term */
+                const double* Lc = tk < S.t_end[v] ? &S.Lo_med[3 * o] : &S.calt_Lo_med[3 * o];
+                for (int c = 0; c < 3; ++c) bud[c] += w * ss * dt * T * fabs(Lc[c]);
+            }
         }
         if (S.unc_prim[v]) {
             /* |L_i(alternative) - L_i(current)| of a near-tie primary ray */
@@ -1261,6 +1503,8 @@ static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb
     out[O_LAMMAX] = fmax(fabs(lam[0]), fmax(fabs(lam[1]), fabs(lam[2])));
     out[O_N_PRIM_UNC] = nprim;
     out[O_N_UNC] = fs.n_unc + fm.n_unc;
+    out[O_N_REPLAYED] = S.n_replayed;
+    out[O_N_BAD_REPLAY] = S.n_bad_replay;
     if (dbg_hit)
         for (int v = 0; v < S.V; ++v) {
             dbg_hit[v] = S.hit[v];
@@ -1283,6 +1527,8 @@ typedef struct {
     int32_t* dbg_hit;
     double *dbg_t, *dbg_margin, *dbg_tie;
     int dbg_stride;
+    const int32_t* replay;
+    int replay_stride;
     volatile int next;
 } job_t;
 
@@ -1295,7 +1541,8 @@ static void* worker(void* arg) {
         int ns = J->n_bands ? 2 * J->n_bands[i] : J->p->n_bins;
         int64_t rec = J->rec_ids ? J->rec_ids[i] : J->p->rec_base + i;
         size_t o = (size_t)i * J->dbg_stride;
-        compute_record(J->s, J->p, ldv(J->pos + 3 * i), nb, ns, rec, J->out + (size_t)i * ORC_OUT_STRIDE,
+        compute_record(J->s, J->p, ldv(J->pos + 3 * i), nb, ns, rec,
+                       J->replay ? J->replay + (size_t)i * J->replay_stride : NULL, J->out + (size_t)i * ORC_OUT_STRIDE,
                        J->dbg_hit ? J->dbg_hit + o : NULL, J->dbg_hit ? J->dbg_t + o : NULL,
                        J->dbg_hit ? J->dbg_margin + o : NULL, J->dbg_hit ? J->dbg_tie + o : NULL);
     }
@@ -1304,11 +1551,14 @@ static void* worker(void* arg) {
 
 /* Compute n records.  rec_ids (nullable) gives each record's jitter index (default
  * rec_base + i); n_bands (nullable) gives per-record band counts with bins = 2 bands.
- * dbg_* (nullable) receive per-ray hit id, t_end, edge margin and tie gap, stride dbg_stride. */
+ * dbg_* (nullable) receive per-ray hit id, t_end, edge margin and tie gap, stride dbg_stride.
+ * replay (nullable): per record, replay_stride primary hit ids (ray order, pole rays last,
+ * -1 = no hit) used instead of the oracle's own closest hits. */
 int orc_records(const orc_scene* s, const orc_params* p, const float* pos, const int64_t* rec_ids,
                 const int32_t* n_bands, int n, double* out, int n_threads, int32_t* dbg_hit, double* dbg_t,
-                double* dbg_margin, double* dbg_tie, int dbg_stride) {
-    job_t J = {s, p, pos, rec_ids, n_bands, n, out, dbg_hit, dbg_t, dbg_margin, dbg_tie, dbg_stride, 0};
+                double* dbg_margin, double* dbg_tie, int dbg_stride, const int32_t* replay, int replay_stride) {
+    job_t J = {s, p, pos, rec_ids, n_bands, n, out, dbg_hit, dbg_t, dbg_margin, dbg_tie, dbg_stride, replay,
+               replay_stride, 0};
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
     pthread_t th[256];
@@ -1324,7 +1574,7 @@ int orc_records(const orc_scene* s, const orc_params* p, const float* pos, const
 int orc_frozen_eval(const orc_scene* s, const orc_params* p, const float* x0f, int64_t rec, const double* x_eval,
                     int n_eval, int which, double* out) {
     shells_t S;
-    build_shells(s, ldv(x0f), p, p->n_bands, p->n_bins, rec, &S);
+    build_shells(s, ldv(x0f), p, p->n_bands, p->n_bins, rec, NULL, &S);
     int k0 = which == 2 ? 1 : 0, k1 = which == 1 ? 0 : S.K;
     for (int e = 0; e < n_eval; ++e) {
         ffsum acc;
