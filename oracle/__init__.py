@@ -25,7 +25,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vrc_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_vrc.so")
-OUT_STRIDE = 128
+OUT_STRIDE = 132
 
 # output slots (see the enum in vrc_oracle.c)
 SLOTS = dict(L=(0, 3), L_ss=(3, 3), L_ms=(6, 3), grad=(9, 9), grad_ss=(18, 9), grad_ms=(27, 9),
@@ -34,7 +34,7 @@ SLOTS = dict(L=(0, 3), L_ss=(3, 3), L_ms=(6, 3), grad=(9, 9), grad_ss=(18, 9), g
              margin_t=(101, 1), n_rays=(102, 1), n_degen=(103, 1), L_ff_ss=(104, 3),
              L_ff_ms=(107, 3), L_Y=(110, 1), lam_max=(111, 1), bud_L=(112, 3), bud_L_ff=(115, 3),
              bud_grad=(118, 3), bud_hess=(121, 3), n_prim_unc=(124, 1), n_unc=(125, 1), n_replayed=(126, 1),
-             n_bad_replay=(127, 1))
+             n_bad_replay=(127, 1), n_lit_replayed=(128, 1), n_unexplained=(129, 1))
 
 
 def build(force: bool = False) -> str:
@@ -74,7 +74,8 @@ def lib():
         _lib.orc_scene_create.restype = P
         _lib.orc_scene_create.argtypes = [P]
         _lib.orc_scene_destroy.argtypes = [P]
-        _lib.orc_records.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, P, P, P, P, C.c_int, P, C.c_int]
+        _lib.orc_records.argtypes = [P, P, P, P, P, C.c_int, P, C.c_int, P, P, P, P, C.c_int, P, C.c_int,
+                                     P, P, P, C.c_int, C.c_int]
         _lib.orc_frozen_eval.argtypes = [P, P, P, C.c_int64, P, C.c_int, C.c_int, P]
         _lib.orc_hg.restype = C.c_double
         _lib.orc_hg.argtypes = [C.c_double, C.c_double]
@@ -165,18 +166,31 @@ def make_params(rp, general_derivs: int = 1, track_margins: int = 0, surface_onl
 
 def records(oscene: OracleScene, rp, pos, rec_ids=None, n_bands=None, n_threads: int = 0,
             debug: bool = False, general_derivs: int = 1, track_margins: int = 0,
-            surface_only: int = 0, replay_hits=None) -> dict:
+            surface_only: int = 0, replay_hits=None, replay_t=None, replay_lit=None) -> dict:
     """Compute records at positions `pos` [n,3] (float32).  Returns named float64 arrays.
 
-    replay_hits (optional, int [n, >= rays]): a primary hit primitive id per ray (ray order,
-    the two pole rays last, -1 = no hit) that the oracle uses instead of its own closest
-    hit; the record is then computed in FP64 on those hits, and no primary-ray decision
-    enters the decision budgets (`n_replayed` counts the rays whose id differed)."""
+    Replay mode (the discrete decisions of a record taken as given, its arithmetic in FP64):
+    replay_hits (int [n, S], S >= rays): a primary hit primitive id per ray (ray order,
+    the two pole rays last, -1 = no hit) used instead of the oracle's own closest hit;
+    no primary-ray decision then enters the decision budgets (`n_replayed` counts the rays
+    whose id differed).  With replay_t (float32 [n, S], each ray's end as computed in FP32:
+    it decides which shell vertices are clamped and which vertices of a cell are furthest)
+    and replay_lit (uint32 [n, shells, ceil(S / 32)], bit v of row k set when vertex v of
+    shell k has radiance: the visibility decisions) every decision is the given one and the
+    budgets are zero; `n_lit_replayed` counts visibility decisions taken the given way (each
+    a shadow ray near an edge here) and `n_unexplained` given decisions that are not near
+    ties in FP64."""
     pos = _f32(pos).reshape(-1, 3)
     n = pos.shape[0]
-    rh = None
+    rh = rt = rl = None
+    n_sh = 0
     if replay_hits is not None:
         rh = np.ascontiguousarray(replay_hits, dtype=np.int32).reshape(n, -1)
+    if replay_t is not None or replay_lit is not None:
+        assert rh is not None and replay_t is not None and replay_lit is not None
+        rt = np.ascontiguousarray(replay_t, dtype=np.float32).reshape(n, rh.shape[1])
+        rl = np.ascontiguousarray(replay_lit).view(np.uint32).reshape(n, -1, (rh.shape[1] + 31) // 32)
+        n_sh = rl.shape[1]
     ids = None if rec_ids is None else np.ascontiguousarray(rec_ids, dtype=np.int64)
     nb = None if n_bands is None else np.ascontiguousarray(n_bands, dtype=np.int32)
     out = np.zeros((n, OUT_STRIDE), np.float64)
@@ -184,19 +198,24 @@ def records(oscene: OracleScene, rp, pos, rec_ids=None, n_bands=None, n_threads:
     if n_threads <= 0:
         n_threads = os.cpu_count() or 1
     stride = 0
-    dh = dt = dm = dtie = None
+    dh = dt = dm = dtie = dl = None
+    dshells = 0
     if debug:
         stride = int((nb.max() * 2 * nb.max() + 2) if nb is not None else rp.n_bands * rp.n_bins + 2)
         dh = np.full((n, stride), -2, np.int32)
         dt, dm, dtie = (np.zeros((n, stride)) for _ in range(3))
+        dshells = int(np.ceil(np.sqrt(3.0) / float(rp.dt))) + 2
+        dl = np.zeros((n, dshells, (stride + 31) // 32), np.uint32)
     lib().orc_records(oscene.ptr, C.byref(p), _p(pos), _p(ids), _p(nb), n, _p(out), n_threads,
-                      _p(dh), _p(dt), _p(dm), _p(dtie), stride, _p(rh), 0 if rh is None else rh.shape[1])
+                      _p(dh), _p(dt), _p(dm), _p(dtie), stride, _p(dl), dshells, _p(rh), _p(rt), _p(rl),
+                      0 if rh is None else rh.shape[1], n_sh)
     res = {k: out[:, a:a + w] if w > 1 else out[:, a] for k, (a, w) in SLOTS.items()}
     res["status"] = res["status"].astype(np.int32)
     res["n_shells"] = res["n_shells"].astype(np.int32)
-    res["n_replayed"] = res["n_replayed"].astype(np.int32)
+    for k in ("n_replayed", "n_lit_replayed", "n_unexplained"):
+        res[k] = res[k].astype(np.int32)
     if debug:
-        res.update(hit_prim=dh, hit_t=dt, hit_margin=dm, hit_tie=dtie)
+        res.update(hit_prim=dh, hit_t=dt, hit_margin=dm, hit_tie=dtie, lit=dl)
     return res
 
 

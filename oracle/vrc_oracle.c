@@ -63,7 +63,7 @@
 #define ORC_PI 3.14159265358979323846
 #define ORC_TMIN 1e-6
 #define ORC_SHADOW_OFFSET 1e-5
-#define ORC_OUT_STRIDE 128
+#define ORC_OUT_STRIDE 132
 
 /* output slots of one record (doubles) */
 enum {
@@ -77,8 +77,26 @@ enum {
      * that flipping every near-tie decision of the record could make */
     O_BUD_L = 112, O_BUD_LFF = 115, O_BUD_G = 118, O_BUD_H = 121, O_N_PRIM_UNC = 124, O_N_UNC = 125,
     /* replay mode: rays whose given primary hit differs from the oracle's own, ids out of range */
-    O_N_REPLAYED = 126, O_N_BAD_REPLAY = 127
+    O_N_REPLAYED = 126, O_N_BAD_REPLAY = 127,
+    /* full replay: visibility decisions taken the given way (each a near tie here), and
+     * given decisions that are not near ties in FP64 (a ray end beyond rounding of the
+     * oracle's, a vertex lit or dark with no shadow ray near an edge) */
+    O_N_LIT_REPLAYED = 128, O_N_UNEXPLAINED = 129
 };
+
+/* The discrete decisions of a record taken from elsewhere (replay mode).  hit: primary hit
+ * id per ray (-1 = none); t: the ray's end as computed in FP32, which then decides the
+ * clamps of shell vertices (open iff t_k < t, both FP32) and the furthest vertices of each
+ * cell (largest such parameter); lit: a bit per (shell, ray), set when the vertex has
+ * radiance, which settles each shadow-ray near tie.  t and lit are used together (full
+ * replay) or not at all; hit may be given alone. */
+typedef struct {
+    const int32_t* hit;
+    const float* t;
+    const uint32_t* lit;
+    int stride;        /* rays per record in hit and t */
+    int shells;        /* rows of lit per record */
+} orc_replay;
 
 /* a discrete decision is "near-tie" when FP32 rounding could flip it */
 #ifndef TIE_EDGE
@@ -857,6 +875,9 @@ int orc_aniso(double LY, const double* h6, double eps, double r_min, double r_ma
 typedef struct {
     int nb, ns, V, N, K;
     int replay;        /* 1: primary hits were given (no primary decision is uncertain) */
+    int full;          /* 1: ray ends and visibility were given too (no decision is uncertain) */
+    double* t_key;     /* [V] the parameter that decides clamps and furthest vertices */
+    int n_lit_replayed, n_unexplained;
     v3 x;
     v3* dir;
     double* t_end;
@@ -890,7 +911,7 @@ static void shells_free(shells_t* S) {
     free(S->dLo_surf); free(S->sLo_surf); free(S->nsh_surf);
     free(S->dLo_med); free(S->sLo_med); free(S->nsh_med);
     free(S->unc_clamp); free(S->calt_Lo_med); free(S->unc_prim);
-    free(S->margin_e); free(S->tie); free(S->t_unc);
+    free(S->margin_e); free(S->tie); free(S->t_unc); free(S->t_key);
     free(S->alt_t); free(S->alt_hit); free(S->alt_Lo_surf); free(S->alt_Lo_med);
 }
 
@@ -907,12 +928,45 @@ static int plane_t(const orc_scene* s, int id, v3 x, v3 d, double* t) {
 /* trace the ray set, the shells and every vertex radiance (Sec. 4, Sec. 6 Implementation).
  * replay (nullable): a primary hit id per ray (-1 = no hit) to use instead of the oracle's
  * own closest hit (reading R16's replay: the reduction is then compared on the same hits). */
+static int lit_bit(const orc_replay* R, int k, int v) {
+    if (k >= R->shells) return 0;
+    int words = (R->stride + 31) / 32;
+    return (int)((R->lit[(size_t)k * words + (size_t)(v >> 5)] >> (v & 31)) & 1u);
+}
+
+/* shell k's parameter t_k as the kernel computes it in FP32 */
+static float tk_f32(int k, float dt) {
+    float a = (float)k - 0.5f;
+    return a * dt;
+}
+
+/* vertex v of shell k >= 1 is open (t_k before its ray's end): FP64, or the given FP32 ends */
+static int vertex_open(const shells_t* S, const orc_params* p, int k, int v) {
+    if (S->full) return tk_f32(k, p->dt) < (float)S->t_key[v];
+    return ((double)k - 0.5) * (double)p->dt < S->t_end[v];
+}
+
+/* a given visibility decision: take the other shadow outcome where it is a near tie */
+static void replay_lit(shells_t* S, int given, double Lo[3], const double sLo[3], int nsh) {
+    int lit = Lo[0] != 0.0 || Lo[1] != 0.0 || Lo[2] != 0.0;
+    if (given == lit) return;
+    if (nsh == 1) {
+        for (int c = 0; c < 3; ++c) Lo[c] += sLo[c];
+        S->n_lit_replayed++;
+    } else {
+        S->n_unexplained++;
+    }
+}
+
 static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, int ns, int64_t rec,
-                         const int32_t* replay, shells_t* S) {
+                         const orc_replay* R, shells_t* S) {
     memset(S, 0, sizeof(*S));
     S->nb = nb; S->ns = ns; S->N = nb * ns; S->V = S->N + 2; S->x = x;
+    const int32_t* replay = R ? R->hit : NULL;
     S->replay = replay != NULL;
-    int V = S->V, track = p->track_margins;
+    S->full = R && R->t && R->lit;
+    int V = S->V, track = p->track_margins || S->full;
+    S->t_key = (double*)malloc(sizeof(double) * V);
     S->dir = (v3*)malloc(sizeof(v3) * V);
     S->t_end = (double*)malloc(sizeof(double) * V);
     S->hit = (int*)malloc(sizeof(int) * V);
@@ -986,6 +1040,14 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
             S->t_end[v] = cube_exit(x, d);
             S->hit[v] = -1;
         }
+        S->t_key[v] = S->t_end[v];
+        if (S->full) {
+            double tg = (double)R->t[v];
+            S->t_key[v] = tg;
+            if (fabs(tg - S->t_end[v]) > fmax(4.0 * S->t_unc[v] * S->t_end[v], 1e-6)) S->n_unexplained++;
+            if (tg > tmax) tmax = tg;
+            replay_lit(S, lit_bit(R, 0, v), &S->Lo_surf[3 * v], &S->sLo_surf[3 * v], S->nsh_surf[v]);
+        }
         S->alt_t[v] = S->t_end[v];
         S->alt_hit[v] = S->hit[v];
         if (S->unc_prim[v]) {
@@ -1016,7 +1078,7 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
         if (S->t_end[v] > tmax) tmax = S->t_end[v];
     }
     double dt = (double)p->dt;
-    S->K = p->surface_only ? 0 : (int)ceil(tmax / dt);
+    S->K = p->surface_only ? 0 : (int)ceil(tmax / dt) + (S->full ? 1 : 0);
     size_t KV = (size_t)(S->K > 0 ? S->K : 1) * V;
     S->Lo_med = (double*)calloc(KV * 3, sizeof(double));
     S->dLo_med = (double*)calloc(KV * 3, sizeof(double));
@@ -1031,12 +1093,18 @@ static void build_shells(const orc_scene* s, v3 x, const orc_params* p, int nb, 
             size_t o = (size_t)(k - 1) * V + v;
             v3 y = add(x, scl(S->dir[v], tk));
             int near = track && fabs(tk - S->t_end[v]) < S->t_unc[v] * S->t_end[v];
-            if (tk < S->t_end[v])
+            int open = vertex_open(S, p, k, v);
+            if (open)
                 medium_radiance(s, y, S->dir[v], &S->Lo_med[3 * o], &S->dLo_med[3 * o], &S->sLo_med[3 * o],
                                 &S->nsh_med[o], track);
             else if (near)      /* clamped now; the alternative is an unclamped medium vertex at t_k */
                 medium_radiance(s, y, S->dir[v], &S->calt_Lo_med[3 * o], NULL, NULL, NULL, 0);
             if (near) S->unc_clamp[o] = 1;
+            if (S->full) {
+                if (open) replay_lit(S, lit_bit(R, k, v), &S->Lo_med[3 * o], &S->sLo_med[3 * o], S->nsh_med[o]);
+                else if (lit_bit(R, k, v)) S->n_unexplained++;     /* given lit, but clamped here */
+                if (open != (tk < S->t_end[v]) && !near) S->n_unexplained++;
+            }
             if (S->unc_prim[v] && tk < S->alt_t[v]) {
                 if (tk < S->t_end[v]) memcpy(&S->alt_Lo_med[3 * o], &S->Lo_med[3 * o], 3 * sizeof(double));
                 else medium_radiance(s, y, S->dir[v], &S->alt_Lo_med[3 * o], NULL, NULL, NULL, 0);
@@ -1113,17 +1181,25 @@ static int far_set_ambiguous(int nearm, int openm) {
     return (nearm & (nearm - 1)) != 0;               /* two or more near-furthest vertices */
 }
 
-/* vertex v of shell k as computed: ray parameter and radiance */
-static double vertex_t(const shells_t* S, const orc_params* p, int k, int v, const double** Lo) {
+/* vertex v of shell k as computed: ray parameter (returned), radiance, and the parameter
+ * that orders it against the cell's other vertices (the same, or in full replay the FP32
+ * value the decisions were taken on) */
+static double vertex_t(const shells_t* S, const orc_params* p, int k, int v, const double** Lo, double* key) {
     static const double zero[3] = {0, 0, 0};
     if (k == 0) {
         *Lo = S->hit[v] >= 0 ? &S->Lo_surf[3 * v] : zero;
+        *key = S->t_key[v];
         return S->t_end[v];
     }
     size_t o = (size_t)(k - 1) * S->V + v;
     double tk = ((double)k - 0.5) * (double)p->dt;
-    if (tk < S->t_end[v]) { *Lo = &S->Lo_med[3 * o]; return tk; }
+    if (vertex_open(S, p, k, v)) {
+        *Lo = &S->Lo_med[3 * o];
+        *key = S->full ? (double)tk_f32(k, p->dt) : tk;
+        return tk;
+    }
     *Lo = zero;                                      /* zero-radiance sample at the occluder (Sec. 4) */
+    *key = S->t_key[v];
     return S->t_end[v];
 }
 
@@ -1336,20 +1412,20 @@ static void ff_accumulate(const orc_scene* s, const shells_t* S, const orc_param
             int vi[3];
             cell_vertices(S->nb, S->ns, c, &vi[0], &vi[1], &vi[2]);
             const double* Lo[3];
-            double t[3];
+            double t[3], key[3];
             v3 y[3];
             for (int q = 0; q < 3; ++q) {
-                t[q] = vertex_t(S, p, k, vi[q], &Lo[q]);
+                t[q] = vertex_t(S, p, k, vi[q], &Lo[q], &key[q]);
                 y[q] = add(S->x, scl(S->dir[vi[q]], t[q]));
             }
             /* furthest vertices (R9): all vertices at the largest t */
-            double tmx = fmax(t[0], fmax(t[1], t[2]));
+            double tmx = fmax(key[0], fmax(key[1], key[2]));
             int nf = 0;
             v3 yf[3];
             const double* Lf[3];
             for (int q = 0; q < 3; ++q)
-                if (t[q] == tmx) { yf[nf] = y[q]; Lf[nf] = Lo[q]; ++nf; }
-            if (p->track_margins) cell_budget(s, S, p, x_eval, k, c, vi, weight, acc);
+                if (key[q] == tmx) { yf[nf] = y[q]; Lf[nf] = Lo[q]; ++nf; }
+            if (p->track_margins && !S->full) cell_budget(s, S, p, x_eval, k, c, vi, weight, acc);
             int dark = 1;
             for (int q = 0; q < nf; ++q)
                 if (Lf[q][0] != 0.0 || Lf[q][1] != 0.0 || Lf[q][2] != 0.0) dark = 0;
@@ -1397,11 +1473,12 @@ static void pack_h6(const double H[3][3], double* o) {
 }
 
 static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb, int ns, int64_t rec,
-                           const int32_t* replay, double* out, int32_t* dbg_hit, double* dbg_t, double* dbg_margin,
-                           double* dbg_tie) {
+                           const orc_replay* replay, double* out, int32_t* dbg_hit, double* dbg_t, double* dbg_margin,
+                           double* dbg_tie, uint32_t* dbg_lit, int dbg_shells, int dbg_stride) {
     memset(out, 0, sizeof(double) * ORC_OUT_STRIDE);
     shells_t S;
     build_shells(s, x, p, nb, ns, rec, replay, &S);
+    const int bud_on = !S.full;           /* in full replay every decision is the given one */
     /* Monte Carlo radiance (Eqs. outLF, mediaLFin, curveLFin with equal-solid-angle strata) */
     v3 wo = ldv(p->omega_o);
     double dt = (double)p->dt, st = s->sigma_t, ss = (double)s->in.sigma_s;
@@ -1414,15 +1491,16 @@ static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb
             double T = exp(-st * S.t_end[v]);
             for (int c = 0; c < 3; ++c) {
                 Lss[c] += w * T * S.Lo_surf[3 * v + c];
-                bud[c] += w * T * S.dLo_surf[3 * v + c];
+                if (bud_on) bud[c] += w * T * S.dLo_surf[3 * v + c];
             }
         }
         for (int k = 1; k <= S.K; ++k) {
             double tk = ((double)k - 0.5) * dt;
             size_t o = (size_t)(k - 1) * S.V + v;
             double T = exp(-st * tk);
-            if (tk < S.t_end[v])
+            if (vertex_open(&S, p, k, v))
                 for (int c = 0; c < 3; ++c) Lms[c] += w * ss * dt * T * S.Lo_med[3 * o + c];
+            if (!bud_on) continue;
             for (int c = 0; c < 3; ++c) bud[c] += w * ss * dt * T * S.dLo_med[3 * o + c];
             if (S.unc_clamp[o]) {   /* the clamp taken the other way adds or removes this vertex's term */
                 const double* Lc = tk < S.t_end[v] ? &S.Lo_med[3 * o] : &S.calt_Lo_med[3 * o];
@@ -1505,6 +1583,8 @@ static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb
     out[O_N_UNC] = fs.n_unc + fm.n_unc;
     out[O_N_REPLAYED] = S.n_replayed;
     out[O_N_BAD_REPLAY] = S.n_bad_replay;
+    out[O_N_LIT_REPLAYED] = S.n_lit_replayed;
+    out[O_N_UNEXPLAINED] = S.n_unexplained;
     if (dbg_hit)
         for (int v = 0; v < S.V; ++v) {
             dbg_hit[v] = S.hit[v];
@@ -1512,6 +1592,17 @@ static void compute_record(const orc_scene* s, const orc_params* p, v3 x, int nb
             dbg_margin[v] = S.margin_e[v];
             dbg_tie[v] = S.tie[v];
         }
+    if (dbg_lit) {      /* the visibility decisions: vertex v of shell k has radiance */
+        int words = (dbg_stride + 31) / 32;
+        for (int k = 0; k <= S.K && k < dbg_shells; ++k)
+            for (int v = 0; v < S.V; ++v) {
+                const double* Lo;
+                double key;
+                vertex_t(&S, p, k, v, &Lo, &key);
+                if (Lo[0] != 0.0 || Lo[1] != 0.0 || Lo[2] != 0.0)
+                    dbg_lit[(size_t)k * words + (v >> 5)] |= 1u << (v & 31);
+            }
+    }
     shells_free(&S);
 }
 
@@ -1527,8 +1618,9 @@ typedef struct {
     int32_t* dbg_hit;
     double *dbg_t, *dbg_margin, *dbg_tie;
     int dbg_stride;
-    const int32_t* replay;
-    int replay_stride;
+    uint32_t* dbg_lit;
+    int dbg_shells;
+    orc_replay replay;
     volatile int next;
 } job_t;
 
@@ -1541,24 +1633,35 @@ static void* worker(void* arg) {
         int ns = J->n_bands ? 2 * J->n_bands[i] : J->p->n_bins;
         int64_t rec = J->rec_ids ? J->rec_ids[i] : J->p->rec_base + i;
         size_t o = (size_t)i * J->dbg_stride;
-        compute_record(J->s, J->p, ldv(J->pos + 3 * i), nb, ns, rec,
-                       J->replay ? J->replay + (size_t)i * J->replay_stride : NULL, J->out + (size_t)i * ORC_OUT_STRIDE,
+        orc_replay R = J->replay;
+        if (R.hit) R.hit += (size_t)i * R.stride;
+        if (R.t) R.t += (size_t)i * R.stride;
+        if (R.lit) R.lit += (size_t)i * R.shells * ((R.stride + 31) / 32);
+        compute_record(J->s, J->p, ldv(J->pos + 3 * i), nb, ns, rec, R.hit ? &R : NULL,
+                       J->out + (size_t)i * ORC_OUT_STRIDE,
                        J->dbg_hit ? J->dbg_hit + o : NULL, J->dbg_hit ? J->dbg_t + o : NULL,
-                       J->dbg_hit ? J->dbg_margin + o : NULL, J->dbg_hit ? J->dbg_tie + o : NULL);
+                       J->dbg_hit ? J->dbg_margin + o : NULL, J->dbg_hit ? J->dbg_tie + o : NULL,
+                       J->dbg_lit ? J->dbg_lit + (size_t)i * J->dbg_shells * ((J->dbg_stride + 31) / 32) : NULL,
+                       J->dbg_shells, J->dbg_stride);
     }
     return NULL;
 }
 
 /* Compute n records.  rec_ids (nullable) gives each record's jitter index (default
  * rec_base + i); n_bands (nullable) gives per-record band counts with bins = 2 bands.
- * dbg_* (nullable) receive per-ray hit id, t_end, edge margin and tie gap, stride dbg_stride.
- * replay (nullable): per record, replay_stride primary hit ids (ray order, pole rays last,
- * -1 = no hit) used instead of the oracle's own closest hits. */
+ * dbg_* (nullable) receive per-ray hit id, t_end, edge margin and tie gap, stride dbg_stride,
+ * and the visibility bits (dbg_lit, zeroed by the caller, dbg_shells rows per record).
+ * Replay (nullable pointers, see orc_replay): per record, replay_stride primary hit ids
+ * (ray order, pole rays last, -1 = no hit), FP32 ray ends, and replay_shells rows of
+ * (replay_stride + 31) / 32 visibility words. */
 int orc_records(const orc_scene* s, const orc_params* p, const float* pos, const int64_t* rec_ids,
                 const int32_t* n_bands, int n, double* out, int n_threads, int32_t* dbg_hit, double* dbg_t,
-                double* dbg_margin, double* dbg_tie, int dbg_stride, const int32_t* replay, int replay_stride) {
-    job_t J = {s, p, pos, rec_ids, n_bands, n, out, dbg_hit, dbg_t, dbg_margin, dbg_tie, dbg_stride, replay,
-               replay_stride, 0};
+                double* dbg_margin, double* dbg_tie, int dbg_stride, uint32_t* dbg_lit, int dbg_shells,
+                const int32_t* replay_hit, const float* replay_t, const uint32_t* replay_lit, int replay_stride,
+                int replay_shells) {
+    orc_replay R = {replay_hit, replay_t, replay_lit, replay_stride, replay_shells};
+    job_t J = {s, p, pos, rec_ids, n_bands, n, out, dbg_hit, dbg_t, dbg_margin, dbg_tie, dbg_stride, dbg_lit,
+               dbg_shells, R, 0};
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
     pthread_t th[256];

@@ -86,3 +86,17 @@ def compare_radius(gpu, ref, idx=None):
         else:
             assert abs(Rg - Ro) <= rel * Ro, (int(i), Rg, Ro, rel)
         assert (st_o & 1) == (st_g & 1), (int(i), st_g, st_o)
+
+
+def oracle_replayed(O, oscene, params, pos, g, rec_ids=None, n_bands=None, idx=None, track_margins=0):
+    """The oracle on the GPU's own discrete decisions (replay mode): its primary hit ids,
+    its FP32 ray ends (which decide the shell clamps and furthest vertices) and its
+    visibility bits, from a launch with debug_hits (parts = 0).  The records are then
+    computed in FP64 on the same decisions and compared with the bare tolerances; every
+    replayed decision must be a near tie for the oracle (n_unexplained == 0)."""
+    sel = slice(None) if idx is None else np.asarray(idx)
+    ref = O.records(oscene, params, pos, rec_ids=rec_ids, n_bands=n_bands, track_margins=track_margins,
+                    replay_hits=g["hit_prim"][sel], replay_t=g["hit_t"][sel], replay_lit=g["dbg_lit"][sel])
+    bad = np.flatnonzero(ref["n_unexplained"] > 0)
+    assert bad.size == 0, f"{bad.size} records with decisions that are not near ties, first {bad[:8]}"
+    return ref

@@ -194,3 +194,80 @@ def test_shell_vertex_at_its_clamp_weighted_ray():
         assert np.all(st["bud_L"][0] <= 4.0 * ch["L"])
         for k in ("grad", "hess"):
             assert np.all(ch[k] <= st[BUD[k]][0]), k
+
+
+def full_replay_inputs(r):
+    """A record's own decisions in the form replay mode takes them: hit ids, FP32 ray ends,
+    visibility bits."""
+    return dict(replay=r["hit_prim"], replay_t=r["hit_t"].astype(np.float32), replay_lit=r["lit"])
+
+
+def record_replayed(tris, x, dec, light=((0.5, 0.5, 0.92), (1.0, 0.9, 0.8))):
+    tris = np.asarray(tris, np.float32)
+    sc = Scene(tris=tris, albedo=np.full((tris.shape[0], 3), 0.7, np.float32), medium=MED,
+               lights=[PointLight(*light)])
+    return O.records(O.OracleScene(sc, use_bvh=False), RP, np.asarray([x], np.float32), n_threads=1,
+                     replay_hits=dec["replay"], replay_t=dec["replay_t"], replay_lit=dec["replay_lit"])
+
+
+def close(a, b, rtol=1e-6):
+    for k in ("L", "grad", "hess", "L_ss", "L_ms"):
+        assert np.allclose(a[k], b[k], rtol=rtol, atol=rtol * np.abs(b[k]).max() + 1e-15), k
+
+
+def test_full_replay_takes_the_given_visibility_and_clamp_decisions():
+    """With every decision given (hits, FP32 ray ends, visibility bits) the oracle computes
+    the record of the side that took them: across a shadow-ray tie, and across the three
+    outcomes of the clamp tie.  Each replayed decision is a near tie here, so none is
+    unexplained, and the budgets are zero."""
+    floor = [[[0, 0, 0.05], [1, 0, 0.05], [1, 1, 0.05]], [[0, 0, 0.05], [1, 1, 0.05], [0, 1, 0.05]]]
+    d = DIRS[100]
+    y = X + d * (2.5 * float(np.float32(0.1)))
+    lp = np.array([0.5, 0.5, 0.92])
+    mid = y + 0.5 * (lp - y)
+    s = (lp - y) / np.linalg.norm(lp - y)
+    g1, g2 = frame(s)
+
+    def scene(delta):
+        return floor + [[mid + delta * g1 - 0.03 * g2, mid + delta * g1 + 0.03 * g2, mid + (delta + 0.05) * g1]]
+
+    a, b = record(scene(3e-7), X), record(scene(-3e-7), X)
+    assert not np.array_equal(a["lit"], b["lit"])
+    ab = record_replayed(scene(3e-7), X, full_replay_inputs(b))
+    assert ab["n_lit_replayed"][0] == 1 and ab["n_unexplained"][0] == 0
+    close(ab, b)
+    for bk in BUD.values():
+        assert np.all(ab[bk][0] == 0)
+
+    dt = float(np.float32(0.1))
+    xz = 2.0 ** -7 + 8 * 2.0 ** -28
+    c = np.float32(xz + 0.5 * dt)
+    x = np.array([0.31, 0.27, xz])
+    light = ((0.5, 0.45, 0.04), (1.0, 0.9, 0.8))
+
+    def ceiling(cc):
+        return [[[0, 0, cc], [1, 0, cc], [0, 1, cc]]]
+
+    sides = {nm: record(ceiling(cc), x, light=light)
+             for nm, cc in (("open", np.nextafter(c, np.float32(1))), ("tied", c),
+                            ("below", np.nextafter(c, np.float32(0))))}
+    for geo, cc in (("open", np.nextafter(c, np.float32(1))), ("below", np.nextafter(c, np.float32(0)))):
+        for nm, st in sides.items():
+            r = record_replayed(ceiling(cc), x, full_replay_inputs(st), light=light)
+            assert r["n_unexplained"][0] == 0, (geo, nm)
+            close(r, st, rtol=2e-6)
+
+
+def test_full_replay_of_own_decisions_changes_nothing(oracle_lib):
+    """Replaying a record's own decisions reproduces it (small workload, all 64 records):
+    the FP32 rounding of the ray ends changes no clamp or furthest-vertex choice here."""
+    import workloads as W
+    w = W.config1()
+    pos = w.positions()
+    osc = O.OracleScene(w.scene)
+    r = O.records(osc, w.params, pos, debug=True)
+    rr = O.records(osc, w.params, pos, replay_hits=r["hit_prim"], replay_t=r["hit_t"].astype(np.float32),
+                   replay_lit=r["lit"])
+    assert np.all(rr["n_replayed"] == 0) and np.all(rr["n_lit_replayed"] == 0) and np.all(rr["n_unexplained"] == 0)
+    for k in ("L", "grad", "hess", "L_ff", "radius"):
+        assert np.allclose(rr[k], r[k], rtol=1e-12, atol=1e-14), k
