@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "records/s (L_i+grad+Hessian) and queries/s at stated oracle error; learned vs plain"
+# the arithmetic of the path: FP32 with the hardware's approximate division and square root
+# and denormals flushed (records, queries), Neumaier-compensated sums, FP64 eigen-solve
+DTYPE = "f32 (-prec-div=false -prec-sqrt=false -ftz=true; compensated sums; f64 eigen-solve)"
 # FP32 operations of one lit cell in the record kernel (FMA = 2, division, square root,
 # exp and atan2 = 1), counted from cell_eval's source for the anisotropic path (g != 0):
 # solid angle and derivatives 318, phase function and derivatives 135, the accumulation
@@ -120,9 +123,9 @@ def measured_peaks():
 K_RECORDS_DRAM_BYTES_PER_RECORD = (65.7088e6 + 3.168768e6) / 1024
 
 
-def fp32_peak_tflops(sm_mhz: float = 2070.0) -> float:
-    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float = 2070.0, n_sm: int = 152) -> float:
+    # SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def flop_per_launch(n_cells: np.ndarray, n_far: np.ndarray) -> float:
@@ -176,6 +179,56 @@ def precision_report(gpu: dict, ref: dict) -> dict:
 
     return {"records": int(n), "L_rel": stats(eL), "grad_rel": stats(eg), "hess_rel": stats(eh),
             "tolerance": {"L_rel": 1e-4, "grad_rel": 1e-3, "hess_rel": 1e-3}}
+
+
+def _fro6(h):
+    return np.sqrt(h[..., 0] ** 2 + h[..., 3] ** 2 + h[..., 5] ** 2 + 2 * (h[..., 1] ** 2 + h[..., 2] ** 2 + h[..., 4] ** 2))
+
+
+def _err_over_allowance(gpu: dict, ref: dict, with_budget: bool):
+    """Per record, the largest of |error| / (tolerance + budget) over L, grad, H and the
+    channels (tolerances 1e-4 relative for L, 1e-3 of the norm for grad and H)."""
+    n = ref["L"].shape[0]
+    Lg, Lo = gpu["L"][:n].astype(np.float64), ref["L"]
+    gg, go = gpu["grad"][:n].reshape(n, 3, 3).astype(np.float64), ref["grad"].reshape(n, 3, 3)
+    hg, ho = gpu["hess"][:n].reshape(n, 3, 6).astype(np.float64), ref["hess"].reshape(n, 3, 6)
+    bL = ref["bud_L"] if with_budget else 0.0
+    bg = ref["bud_grad"] if with_budget else 0.0
+    bh = ref["bud_hess"] if with_budget else 0.0
+    rL = np.abs(Lg - Lo) / (1e-4 * np.abs(Lo) + bL + 1e-12)
+    rg = np.linalg.norm(gg - go, axis=2) / (1e-3 * np.linalg.norm(go, axis=2) + bg + 1e-12)
+    rh = _fro6(hg - ho) / (1e-3 * _fro6(ho) + bh + 1e-12)
+    return np.maximum(np.maximum(rL.max(1), rg.max(1)), rh.max(1))
+
+
+def decision_report(gpu_dbg: dict, replayed: dict, own: dict) -> dict:
+    """Every record against the FP64 oracle (1) on the GPU's own discrete decisions (replay
+    mode: primary hits, FP32 ray ends, visibility bits), bare tolerances; (2) on the oracle's
+    own decisions, with each record's decision budget (the change its near-tie decisions can
+    make); and the conditioning kappa = sum of per-cell Hessian norms / norm of their sum."""
+    n = own["L"].shape[0]
+    r1 = _err_over_allowance(gpu_dbg, replayed, False)
+    r_bare = _err_over_allowance(gpu_dbg, own, False)
+    r_bud = _err_over_allowance(gpu_dbg, own, True)
+    Lo, go, ho = own["L"], own["grad"].reshape(n, 3, 3), own["hess"].reshape(n, 3, 6)
+    bud_tol = np.maximum(np.maximum((own["bud_L"] / (1e-4 * np.abs(Lo) + 1e-12)).max(1),
+                                    (own["bud_grad"] / (1e-3 * np.linalg.norm(go, axis=2) + 1e-12)).max(1)),
+                         (own["bud_hess"] / (1e-3 * _fro6(ho) + 1e-12)).max(1))
+    nz = (own["bud_L"].max(1) > 0) | (own["bud_grad"].max(1) > 0) | (own["bud_hess"].max(1) > 0)
+    kap = own["kappa"][np.isfinite(own["kappa"])]
+    return {"replay": {"records": int(n), "within_tolerance": int((r1 <= 1).sum()),
+                       "max_err_over_tol": float(r1.max()),
+                       "rays_with_other_hit": int(replayed["n_replayed"].sum()),
+                       "visibility_decisions_replayed": int(replayed["n_lit_replayed"].sum()),
+                       "unexplained_decisions": int(replayed["n_unexplained"].sum())},
+            "own_decisions": {"records": int(n), "within_bare_tolerance": int((r_bare <= 1).sum()),
+                              "within_tolerance_plus_budget": int((r_bud <= 1).sum()),
+                              "max_err_over_tol_plus_budget": float(r_bud.max()),
+                              "records_with_budget": int(nz.sum()),
+                              "budget_over_tol": {"max": float(bud_tol.max()), "p99": float(np.percentile(bud_tol, 99)),
+                                                  "median": float(np.median(bud_tol))}},
+            "kappa": {"max": float(kap.max()), "p99": float(np.percentile(kap, 99)),
+                      "median": float(np.median(kap))}}
 
 
 def run_reference(args, w, rank, world):
@@ -301,74 +354,59 @@ def run_gpu(args, w, rank, world, local_rank):
     line = None
     if rank == 0:
         gpu_rec = {k: rec[k].cpu().numpy() for k in ("L", "grad", "hess")}
+        gpu_dbg = None
+        if not args.no_cpu_baseline:
+            # the same records once more with their discrete decisions written out (after the
+            # timed region), for the comparison with the oracle on the GPU's own decisions
+            dbg = vrc.compute_records(scene, pos, rp, debug_hits=True)
+            gpu_dbg = {k: v.cpu().numpy() for k, v in dbg.items() if k in ("L", "grad", "hess", "hit_prim", "hit_t",
+                                                                            "dbg_lit")}
         line = report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h,
-                      kernel_ms, gpu_rec)
+                      kernel_ms, gpu_rec, gpu_dbg)
     return line
 
 
 def e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, flush):
+    """The same step through the library's host-buffer C-ABI call (vrc_cache_step_host):
+    positions and query points in page-locked host memory, the records and the answers
+    back in page-locked host memory, every copy inside the timed call (the library uploads
+    the queries while the records compute and downloads the records while the grid and
+    the queries run, on a second stream of its own)."""
     import torch
+    n, nq = w.n_records, w.n_queries
     h_pos = torch.from_numpy(pos_np).pin_memory()
     h_q = torch.from_numpy(q_np).pin_memory()
-    h_rgb = torch.empty((w.n_queries, 3), dtype=torch.float32).pin_memory()
-    h_cnt = torch.empty((w.n_queries,), dtype=torch.int32).pin_memory()
-    h_out = {k: torch.empty(rec[k].shape, dtype=rec[k].dtype).pin_memory() for k in ("L", "grad", "hess", "radius")}
-    d_pos = torch.empty_like(pos)
-    d_q = torch.empty_like(q)
-
-    grids = []
-    side = torch.cuda.Stream()       # copies that overlap the kernels of the main stream
-
-    def e2e_step():
-        main = torch.cuda.current_stream()
-        side.wait_stream(main)
-        d_pos.copy_(h_pos, non_blocking=True)
-        with torch.cuda.stream(side):            # the queries arrive while the records compute
-            d_q.copy_(h_q, non_blocking=True)
-            q_in = torch.cuda.Event()
-            q_in.record(side)
-        vrc.compute_records(scene, d_pos, rp, out=rec)
-        rec_done = torch.cuda.Event()
-        rec_done.record(main)
-        with torch.cuda.stream(side):            # the records leave while the grid and queries run
-            side.wait_event(rec_done)
-            for k, v in h_out.items():
-                v.copy_(rec[k], non_blocking=True)
-        if grids:
-            grid = grids[0].rebuild(rec)
-        else:
-            grid = vrc.Grid(rec, extrap_order=rp.extrap_order)
-            grids.append(grid)
-        main.wait_event(q_in)
-        vrc.query_inscatter(grid, d_q, rgb, cnt)
-        h_rgb.copy_(rgb, non_blocking=True)
-        h_cnt.copy_(cnt, non_blocking=True)
-        main.synchronize()
-        side.synchronize()
-        return grid
-
+    out = {"L": torch.empty((n, 3), dtype=torch.float32).pin_memory(),
+           "grad": torch.empty((n, 9), dtype=torch.float32).pin_memory(),
+           "hess": torch.empty((n, 18), dtype=torch.float32).pin_memory(),
+           "radius": torch.empty((n,), dtype=torch.float32).pin_memory(),
+           "rgb": torch.empty((nq, 3), dtype=torch.float32).pin_memory(),
+           "qstatus": torch.empty((nq,), dtype=torch.int32).pin_memory()}
+    step = vrc.HostStep(scene, rp)
     for _ in range(2):
-        e2e_step()
+        step(h_pos, h_q, out)
     e2e_t = []
-    for _ in range(max(1, min(args.steps, 5))):
+    for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_step()
+        step(h_pos, h_q, out)                   # synchronous: returns with every output on the host
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e_t))
     h2d = h_pos.numel() * 4 + h_q.numel() * 4
-    d2h = sum(v.numel() * 4 for v in h_out.values()) + h_rgb.numel() * 4 + h_cnt.numel() * 4
+    d2h = sum(v.numel() * 4 for v in out.values())
     return e2e_s, h2d, d2h
 
 
 def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h, kernel_ms,
-           gpu_rec=None):
+           gpu_rec=None, gpu_dbg=None):
     value = world * w.n_records / (ms * 1e-3)
     if True:
         clk = clocks.summary()
         peaks = measured_peaks()
-        fp32_peak = fp32_peak_tflops(2070.0)
+        import torch
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        fp32_peak = fp32_peak_tflops(2070.0, n_sm)
         flop = flop_per_launch(n_cells, n_far)
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0)) if peaks else 6800.0
         q_gbs = (28.0 * w.n_queries + 64.0 * w.n_records) / (q_ms * 1e-3) / 1e9
@@ -377,7 +415,7 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
         achieved = flop / (kernel_ms[1] * 1e-3) / 1e12
         line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32 (f64 eigen-solve)", "data": "synthetic",
+                "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
                 "config": {"workload": w.name, "records": w.n_records, "rays_per_record": w.params.n_rays,
                            "queries": w.n_queries, "scene_tris": w.scene.n_tris,
                            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -393,7 +431,7 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                              "traffic": K_RECORDS_DRAM_BYTES_PER_RECORD * w.n_records,
                              "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1,024-record "
                                                "launch of this workload, scaled by records",
-                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                             "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x 2070 MHz",
                              "lit_cells_per_launch": int(n_cells.sum()), "far_vertex_evals": int(n_far.sum()),
                              "flop_per_launch": flop},
                 "query_roofline": {"kernel": "k_query", "bound": "hbm", "achieved": q_gbs, "peak": hbm_peak,
@@ -405,8 +443,9 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                 "e2e": None if math.isnan(e2e_s) else
                 {"value": world * w.n_records / e2e_s, "unit": "records/s", "h2d_bytes_per_step": int(h2d),
                  "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
-                 "path": "pinned host -> compute_records -> build_record_grid -> query_inscatter -> pinned host; "
-                         "the query upload and the record download overlap the kernels on a second stream"},
+                 "path": "vrc_cache_step_host (one C-ABI call per step): page-locked host positions and points "
+                         "in, records and answers out; the library overlaps the query upload and the record "
+                         "download with the kernels on a second stream"},
                 "gpu_launches": None,
                 "record_status": {"ok": int((st == 0).sum()), "clamped": int(((st & 6) != 0).sum()),
                                   "nonfinite": int(((st & 1) != 0).sum())},
@@ -433,6 +472,14 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
             if gpu_rec is not None:
                 # the oracle just computed the same 4,096 records (positions, jitter indices)
                 line["precision_vs_oracle"] = precision_report(gpu_rec, oracle_rates.last_records)
+                if gpu_dbg is not None:
+                    import oracle
+                    osc = oracle.OracleScene(w.scene)
+                    pos = w.positions()
+                    replayed = oracle.records(osc, w.params, pos, replay_hits=gpu_dbg["hit_prim"],
+                                              replay_t=gpu_dbg["hit_t"], replay_lit=gpu_dbg["dbg_lit"])
+                    own = oracle.records(osc, w.params, pos, track_margins=1)
+                    line["precision_vs_oracle"]["decisions"] = decision_report(gpu_dbg, replayed, own)
         print(json.dumps(line), flush=True)
     return line
 
@@ -470,7 +517,7 @@ def run_batching(args, w):
     rays = float((2 * w.band_counts.astype(np.float64) ** 2 + 2).sum())
     line = {"metric": METRIC, "value": w.n_records / (res["graph"] * 1e-3), "unit": "records/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["graph"], "higher_is_better": True,
-            "dtype": "f32 (f64 eigen-solve)", "data": "synthetic",
+            "dtype": DTYPE, "data": "synthetic",
             "config": {"workload": w.name, "records": w.n_records, "scene_tris": w.scene.n_tris,
                        "primary_rays": rays, "l2": "scene 6 MB BVH; inputs 1.2 MB"},
             "plain_ms": res["plain"], "graph_ms": res["graph"], "tuning": best, "autotune_s": tune_s,
@@ -518,7 +565,7 @@ def run_flat(args, w):
     cpu_s = time.perf_counter() - t0
     line = {"metric": METRIC, "value": w.n_records / (step_ms * 1e-3), "unit": "records/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "dtype": "f32 (f64 eigen-solve)", "data": "synthetic",
+            "dtype": DTYPE, "data": "synthetic",
             "config": {"workload": w.name, "records": w.n_records, "directions": w.params.n_bins,
                        "segments": w.scene.n_segs, "queries": int(q.shape[0])},
             "records_ms": rec_ms, "records_per_s_kernel": w.n_records / (rec_ms * 1e-3),

@@ -58,6 +58,7 @@ typedef struct { float pos[3]; float intensity[3]; } vrc_point_light;
 #define VRC_MAX_LIGHTS 4
 
 typedef struct vrc_scene vrc_scene;
+typedef struct vrc_grid vrc_grid;   /* record lookup structure (vrc_build_record_grid) */
 
 /* Build a scene: uploads the triangles, builds a bounding volume hierarchy on the
  * host and keeps it on the device.  verts_xyz [n_verts][3], tri_idx [n_tris][3]
@@ -122,7 +123,12 @@ typedef struct {
  *                   the order of eig, clamped to [r_min, r_max]; NULL to skip
  *   axes [n][9]     the matching unit eigenvectors, row i for eig[i] (FP64 solve, stored
  *                   as float); NULL to skip.  Eigenvectors of equal eigenvalues are any
- *                   orthonormal basis of their eigenspace (the ellipsoid is unique). */
+ *                   orthonormal basis of their eigenspace (the ellipsoid is unique).
+ *   dbg_lit [n][dbg_shells][(dbg_stride + 31) / 32]  (debug, NULL to skip; needs hit_prim)
+ *                   bit v of row k is set when vertex v of shell k (k = 0 the surface
+ *                   shell, k >= 1 medium shell k; rays in hit_prim's order) has nonzero
+ *                   radiance: the record's visibility decisions.  The caller zeroes the
+ *                   buffer; shells k >= dbg_shells are not written. */
 typedef struct {
     float* L;
     float* grad;
@@ -148,6 +154,8 @@ typedef struct {
     int32_t dbg_stride;
     float* radii;
     float* axes;
+    uint32_t* dbg_lit;
+    int32_t dbg_shells;
 } vrc_records_view;
 
 /* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default: 384
@@ -183,6 +191,21 @@ int vrc_compute_records(vrc_scene* scene, const float* d_pos, int32_t n, const i
  * in and out through device buffers owned by the scene; synchronous. */
 int vrc_compute_records_host(vrc_scene* scene, const float* h_pos, int32_t n, const vrc_record_params* params,
                              float* h_L, float* h_grad, float* h_hess, float* h_radius, int32_t* h_status);
+
+/* One whole step of the cache from HOST buffers (Secs. 4-6: records, then queries by
+ * Eq. radianceTaylor): h_pos [n][3] in -> records as vrc_compute_records (parts and
+ * extrap_order from params) -> the record grid -> nq queries h_q [nq][3] -> h_rgb [nq][3]
+ * and h_qstatus [nq] (as vrc_query_inscatter), and the records h_L [n][3], h_grad [n][9],
+ * h_hess [n][18], h_radius [n], h_status [n] (each may be NULL).  *grid: NULL on the first
+ * call, which builds the grid and stores it there (the caller frees it with
+ * vrc_destroy_grid); later calls rebuild it in place.  The copies run in device buffers
+ * and on two streams owned by the scene: the queries are uploaded while the records are
+ * computed, the records downloaded while the grid and the queries run; host buffers must
+ * be page-locked for the copies to overlap.  Synchronous: every output is in host memory
+ * on return.  VRC_ERR_INVALID for bad sizes or null buffers, else as the calls it makes. */
+int vrc_cache_step_host(vrc_scene* scene, vrc_grid** grid, const float* h_pos, int32_t n,
+                        const vrc_record_params* params, const float* h_q, int32_t nq, float* h_L, float* h_grad,
+                        float* h_hess, float* h_radius, int32_t* h_status, float* h_rgb, int32_t* h_qstatus);
 
 int vrc_set_record_tuning(vrc_scene* scene, const vrc_record_tuning* tuning);
 int vrc_get_record_tuning(const vrc_scene* scene, vrc_record_tuning* tuning);
@@ -220,7 +243,6 @@ int vrc_graph_launch(vrc_graph* graph, void* stream);
 void vrc_graph_destroy(vrc_graph* graph);
 
 /* --------------------------------------------------------------- queries */
-typedef struct vrc_grid vrc_grid;
 
 /* Build the lookup structure for Eq. radianceTaylor from n device records (pos,
  * radius, L, grad and, for extrap_order 2, hess of `recs`): a compact record table
@@ -282,8 +304,9 @@ void vrc2d_destroy_scene(vrc2d_scene* scene);
  * (Eq. radiusAniso2D per eigenvalue) with the plane's normal as third axis (radius
  * r_max), so vrc_build_record_grid(_aniso) and vrc_query_inscatter answer 2D queries at
  * z = 0.5.  params->parts selects surface shell / medium shells as for 3D records.
- * Asynchronous on `stream`.  VRC_ERR_INVALID for bad parameters; VRC_ERR_UNSUPPORTED for
- * more than 4096 directions. */
+ * out->hit_prim / hit_t (debug, nullable) receive each ray's hit segment (-1 = none) and
+ * t at [rec][ray], dbg_stride >= N.  Asynchronous on `stream`.  VRC_ERR_INVALID for bad
+ * parameters; VRC_ERR_UNSUPPORTED for more than 4096 directions. */
 int vrc2d_compute_records(vrc2d_scene* scene, const float* d_pos, int32_t n, const vrc_record_params* params,
                           const vrc_records_view* out, void* stream);
 
@@ -352,6 +375,24 @@ int vrc_init_levels(const int32_t* d_valid, int32_t n, int32_t start_level, int3
 /* d_level[i] = -1 (leaves the candidate pool) where d_count[i] > 0.  Asynchronous. */
 int vrc_update_coverage(const int32_t* d_count, int32_t n, int32_t* d_level, void* stream);
 
+/* d_level[i] = -1 where d_level[i] == level: the candidates of one level leave a (copy of
+ * the) pool, so that site selection level by level picks each candidate at its own level
+ * only (one-shot placement).  Asynchronous. */
+int vrc_retire_level(int32_t* d_level, int32_t n, int32_t level, void* stream);
+
+/* Fallback rule of the learned radius (not in the paper): the predicted radius R^ =
+ * exp(d_logr[i] + logr_offset) (the offset carries a prediction made at the training
+ * tolerance eps0 to eps: R goes as eps^(1/5) by Eq. radiusAniso3D, so the offset is
+ * log(eps / eps0) / 5) is kept only where a record of the coarse ray set at the same
+ * point says its error is within the tolerance -- the error at R of Eq. radiusAniso3D,
+ * 4 pi |lambda| R^5 / (15 L), is at most eps exactly when R is at most that coarse
+ * record's radius d_radius_coarse[i] (computed at eps).  Elsewhere d_logr_out[i] =
+ * logr_fallback (a caller's value that sends the candidate to plain placement) and
+ * *d_n_fallback (device, caller-zeroed) is incremented.  d_radius_coarse NULL: the offset
+ * only.  Asynchronous. */
+int vrc_mlp_fallback(const float* d_logr, int32_t n, float logr_offset, const float* d_radius_coarse,
+                     float logr_fallback, float* d_logr_out, int32_t* d_n_fallback, void* stream);
+
 /* Learned placement level of each pool candidate from a predicted log radius: the finest
  * level whose cell is at most cell_over_radius x the predicted radius, in [lmin, lmax]. */
 int vrc_levels_from_radius(const float* d_logr, int32_t n, float cell_over_radius, int32_t lmin, int32_t lmax,
@@ -404,16 +445,21 @@ int vrc_mlp_status(const vrc_mlp* mlp);
  * device memory and hands out fixed pools, a real-time renderer that forbids
  * allocation after start-up because cudaMalloc may synchronise the device and stall
  * its other streams, a service with a hard pre-reserved memory budget.  This entry
- * point answers the same queries (same Eq. radianceTaylor, same results within float
- * rounding) straight from the caller's record buffers and allocates nothing: no
- * cudaMalloc, cudaFree or allocating library routine.  Its working memory is one
- * file-scope device array of VRC_NOALLOC_SCRATCH_INTS 32-bit words (4 MiB) that every
- * GPU loading the library holds until the process exits.
+ * point answers the same queries as a grid of sphere records from vrc_build_record_grid
+ * (same Eq. radianceTaylor, same results within float rounding) straight from the
+ * caller's record buffers and allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine.  Ellipsoidal regions are not served: the radii and axes fields are
+ * ignored and each record's sphere of radius R_k is used.  Its working memory is one
+ * file-scope device array of VRC_NOALLOC_SCRATCH_INTS 32-bit words (4 MiB).
  *   recs     device records: pos, radius, L, grad (and hess for extrap_order 2)
  *   n        number of records, at most VRC_NOALLOC_MAX_RECORDS (else VRC_ERR_UNSUPPORTED)
  *   d_q, nq, d_rgb, d_status   as for vrc_query_inscatter
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every
+ * with that device current.  CUDA loads a library's device code lazily by default, so
+ * that first call may also load the module and reserve the array on the device, which
+ * can synchronise the device or fail (VRC_ERR_CUDA) when memory is short: make the first
+ * call during start-up, before any stream capture.  From then on the device holds the
+ * array until the process exits.  Every
  * call reuses the same array and leaves its contents behind, so two calls that overlap
  * on the GPU (different streams without ordering, or concurrent host threads) race and
  * may return wrong results: order them on one stream.  If the record lists do not fit

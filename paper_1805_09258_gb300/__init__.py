@@ -11,6 +11,7 @@ compute_records_host, build_record_grid, query_inscatter.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from typing import Optional
 
@@ -47,7 +48,7 @@ class RecordsView(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms",
                                            "hess_ms", "L_ff", "radius", "eig", "kappa", "status", "pos",
                                            "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t")] + [("dbg_stride", C.c_int32)] + \
-        [("radii", C.c_void_p), ("axes", C.c_void_p)]
+        [("radii", C.c_void_p), ("axes", C.c_void_p), ("dbg_lit", C.c_void_p), ("dbg_shells", C.c_int32)]
 
 
 class RecordTuning(C.Structure):
@@ -73,6 +74,7 @@ def load_library(path: Optional[str] = None):
     L.vrc_destroy_scene.restype = None
     L.vrc_compute_records.argtypes = [P, P, I32, P, P, P, P]
     L.vrc_compute_records_host.argtypes = [P, P, I32, P, P, P, P, P, P]
+    L.vrc_cache_step_host.argtypes = [P, C.POINTER(C.c_void_p), P, I32, P, P, I32, P, P, P, P, P, P, P]
     L.vrc_set_record_tuning.argtypes = [P, P]
     L.vrc_record_timing.argtypes = [P, I32]
     L.vrc_record_kernel_times.argtypes = [P, P, P]
@@ -105,6 +107,8 @@ def load_library(path: Optional[str] = None):
     L.vrc_compact_indices.argtypes = [P, I32, P, C.c_int64, P, P, P]
     L.vrc_levels_by_cell.argtypes = [P, I32, I32, P, P, P, I32, C.c_float, I32, I32, P, P, P]
     L.vrc_levels_from_radius.argtypes = [P, I32, C.c_float, I32, I32, P, P]
+    L.vrc_retire_level.argtypes = [P, I32, I32, P]
+    L.vrc_mlp_fallback.argtypes = [P, I32, C.c_float, P, C.c_float, P, P, P]
     L.vrc_mlp_create.argtypes = [P, C.POINTER(C.c_void_p)]
     L.vrc_mlp_destroy.argtypes = [P]
     L.vrc_mlp_destroy.restype = None
@@ -246,9 +250,11 @@ def records_view(out: dict, dbg_stride: int = 0) -> RecordsView:
     v = RecordsView()
     for k in ("L", "grad", "hess", "L_ss", "grad_ss", "hess_ss", "L_ms", "grad_ms", "hess_ms", "L_ff", "radius",
               "eig", "kappa", "status", "pos", "n_cells", "n_far", "n_shells", "log_radius", "hit_prim", "hit_t",
-              "radii", "axes"):
+              "radii", "axes", "dbg_lit"):
         setattr(v, k, _ptr(out.get(k)))
     v.dbg_stride = dbg_stride
+    if out.get("dbg_lit") is not None:
+        v.dbg_shells = int(out["dbg_lit"].shape[1])
     return v
 
 
@@ -267,6 +273,10 @@ def compute_records(scene: Scene, pos, params, n_bands=None, out: Optional[dict]
         stride = nb * ns + 2
         out["hit_prim"] = torch.full((n, stride), -2, dtype=torch.int32, device=pos.device)
         out["hit_t"] = torch.zeros((n, stride), dtype=torch.float32, device=pos.device)
+        # visibility decisions: a bit per (shell, ray); every ray ends inside the unit cube,
+        # so shells beyond ceil(sqrt(3) / dt) hold no open vertex
+        shells = int(math.ceil(math.sqrt(3.0) / float(params.dt))) + 2
+        out["dbg_lit"] = torch.zeros((n, shells, (stride + 31) // 32), dtype=torch.int32, device=pos.device)
     v = records_view(out, stride)
     p = record_params(params)
     nbp = None
@@ -319,15 +329,20 @@ class Scene2D:
 
 
 def compute_records_2d(scene: Scene2D, pos, params, out: Optional[dict] = None, full: bool = True,
-                       stream=None) -> dict:
+                       debug_hits: bool = False, stream=None) -> dict:
     """vrc2d_compute_records on device positions pos [n, 2]: records in the 3D layout in
-    the plane z = 0.5 (see vrc.h)."""
+    the plane z = 0.5 (see vrc.h).  debug_hits: also each ray's hit segment and t."""
     torch = _torch()
     assert pos.is_cuda and pos.dtype == torch.float32 and pos.is_contiguous() and pos.shape[1] == 2
     n = pos.shape[0]
     if out is None:
         out = alloc_records(n, full=full, device=pos.device)
-    v = records_view(out)
+    stride = 0
+    if debug_hits:
+        stride = int(params.n_bins)
+        out["hit_prim"] = torch.full((n, stride), -2, dtype=torch.int32, device=pos.device)
+        out["hit_t"] = torch.zeros((n, stride), dtype=torch.float32, device=pos.device)
+    v = records_view(out, stride)
     p = record_params(params)
     rc = load_library().vrc2d_compute_records(scene.handle, _ptr(pos), n, C.byref(p), C.byref(v),
                                               _stream_ptr(stream))
@@ -385,6 +400,48 @@ def compute_records_host(scene: Scene, pos: np.ndarray, params) -> dict:
                                                  res["status"].ctypes.data)
     _check(rc, "vrc_compute_records_host")
     return res
+
+
+def _host_ptr(a):
+    """Address of a host buffer: a numpy array or a (page-locked) torch CPU tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert not a.is_cuda and a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+class HostStep:
+    """vrc_cache_step_host: one whole step from host buffers -- records at host positions,
+    the record grid (built on the first call, rebuilt in place after), queries at host
+    points -- with the copies inside the call.  Host buffers may be numpy arrays or
+    page-locked torch CPU tensors (the copies overlap the kernels only when page-locked)."""
+
+    def __init__(self, scene: "Scene", params):
+        self.scene = scene
+        self.params = params
+        self._grid = C.c_void_p()
+
+    def __call__(self, pos, q, out: dict) -> dict:
+        """pos [n, 3], q [nq, 3] float32 host buffers; out: host buffers L [n, 3], grad [n, 9],
+        hess [n, 18], radius [n], status [n] (any may be missing), rgb [nq, 3], qstatus [nq]."""
+        n, nq = int(pos.shape[0]), int(q.shape[0])
+        p = record_params(self.params)
+        rc = load_library().vrc_cache_step_host(self.scene.handle, C.byref(self._grid), _host_ptr(pos), n,
+                                                C.byref(p), _host_ptr(q), nq,
+                                                *[_host_ptr(out.get(k)) for k in ("L", "grad", "hess", "radius",
+                                                                                  "status", "rgb", "qstatus")])
+        _check(rc, "vrc_cache_step_host")
+        return out
+
+    def __del__(self):
+        try:
+            if self._grid:
+                load_library().vrc_destroy_grid(self._grid)
+        except Exception:
+            pass
 
 
 class Grid:
@@ -452,8 +509,10 @@ def query_inscatter_noalloc(records: dict, q, n: Optional[int] = None, extrap_or
 
     For callers that cannot allocate device memory at query time: the library uses a
     fixed 4 MiB device array instead of cudaMalloc.  Calls that overlap on the GPU race
-    on that array; keep them ordered on one stream.  The first call on a device should
-    come before any stream capture.
+    on that array; keep them ordered on one stream.  The first call on a device may load
+    the library's device code and reserve the array (CUDA loads modules lazily): make it
+    during start-up, before any stream capture.  Sphere records only (radii and axes are
+    ignored).
     """
     torch = _torch()
     assert q.is_cuda and q.dtype == torch.float32 and q.is_contiguous()
@@ -641,6 +700,26 @@ def init_levels(valid, level, start_level: int, stream=None):
 def update_coverage(count, level, stream=None):
     _check(load_library().vrc_update_coverage(_ptr(count), count.shape[0], _ptr(level), _stream_ptr(stream)),
            "vrc_update_coverage")
+
+
+def retire_level(level, lv: int, stream=None):
+    _check(load_library().vrc_retire_level(_ptr(level), level.shape[0], lv, _stream_ptr(stream)), "vrc_retire_level")
+
+
+def mlp_fallback(logr, logr_offset: float, radius_coarse, logr_fallback: float, out=None, n_fallback=None,
+                 stream=None):
+    """vrc_mlp_fallback: the predicted log radius shifted by logr_offset, kept only where
+    the coarse record's radius is at least that (radius_coarse None: shift only); returns
+    (logr_out, n_fallback device int32[1])."""
+    torch = _torch()
+    n = logr.shape[0]
+    out = torch.empty_like(logr) if out is None else out
+    if n_fallback is None:
+        n_fallback = torch.zeros((1,), dtype=torch.int32, device=logr.device)
+    _check(load_library().vrc_mlp_fallback(_ptr(logr), n, float(logr_offset), _ptr(radius_coarse),
+                                           float(logr_fallback), _ptr(out), _ptr(n_fallback), _stream_ptr(stream)),
+           "vrc_mlp_fallback")
+    return out, n_fallback
 
 
 def levels_from_radius(logr, level, cell_over_radius: float, lmin: int, lmax: int, stream=None):

@@ -136,9 +136,17 @@ __device__ __forceinline__ int cell_eval(const float3 (&r)[3], const float (&t)[
     float rho[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) rho[q] = sqrtf(dot3(r[q], r[q]));
-    float3 e1 = r[1] - r[0], e2 = r[2] - r[0];
-    float3 nrm = cross3(e1, e2);
-    float A = dot3(r[0], nrm);
+    // The plane normal (the same vector from any vertex, cyclic order kept) is taken from
+    // the vertex nearest to x: from a far vertex of a sliver cell across a depth
+    // discontinuity the two edges are long and nearly parallel, and their cross product
+    // cancels in FP32 (a few percent of such a cell's Hessian near a surface).
+    const bool b0 = rho[0] <= rho[1] && rho[0] <= rho[2];
+    const bool b1 = !b0 && rho[1] <= rho[2];
+    const float3 rb = b0 ? r[0] : (b1 ? r[1] : r[2]);
+    const float3 rn = b0 ? r[1] : (b1 ? r[2] : r[0]);
+    const float3 rp = b0 ? r[2] : (b1 ? r[0] : r[1]);
+    float3 nrm = cross3(rn - rb, rp - rb);
+    float A = dot3(rb, nrm);
     float3 a = nrm * -1.0f;
     if (!ff_signed && A < 0.f) { A = -A; a = nrm; }
     float d01 = dot3(r[0], r[1]), d12 = dot3(r[1], r[2]), d02 = dot3(r[0], r[2]);
@@ -381,6 +389,13 @@ __device__ __noinline__ void write_ellipsoid(const double h[6], const double lam
     }
 }
 
+// debug output: vertex gv of shell k of record rec has radiance (the visibility decisions)
+__device__ __forceinline__ void dbg_set_lit(const vrc_records_view& o, int rec, int k, int gv) {
+    if (k >= o.dbg_shells) return;
+    const int words = (o.dbg_stride + 31) >> 5;
+    atomicOr(&o.dbg_lit[((size_t)rec * o.dbg_shells + k) * words + (gv >> 5)], 1u << (gv & 31));
+}
+
 // ----------------------------------------------------------------- the kernel
 // Registers are capped at 85 per thread: 24 warps per SM, as 3 blocks of 256 (band chunks
 // sized so three blocks' shared memory fits) or 2 blocks of 384 (a whole ray set that fits
@@ -522,6 +537,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                 tmax_loc = fmaxf(tmax_loc, te);
                 te_b = te;
                 const bool owned = lv < (r1 - r0) * ns;        // a vertex of the rows this chunk owns
+                if (a.out.dbg_lit && lit_v && (owned || (pole && ((lv == PN && north) || (lv == PS && south)))))
+                    dbg_set_lit(a.out, rec, 0, gv);
                 if (owned && prim >= 0) {
                     float w = wmc * hg_dev(-dot3(d, a.wo), g) * __expf(-sigma_t * te);
                     neumaier(mc[0], mcc[0], w * Lo.x);
@@ -817,6 +834,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                             Lrn[a.cap + lv] = Lo.y;
                             Lrn[2 * a.cap + lv] = Lo.z;
                             lit_v = Lo.x != 0.f || Lo.y != 0.f || Lo.z != 0.f;
+                            if (a.out.dbg_lit && lit_v) {
+                                const bool pole = lv >= rows * ns;
+                                if (!pole ? lv < (r1 - r0) * ns : ((lv == PN && north) || (lv == PS && south)))
+                                    dbg_set_lit(a.out, rec, k + 1, !pole ? r0 * ns + lv : (lv == PN ? N : N + 1));
+                            }
                         }
                         const unsigned lmk = __ballot_sync(0xffffffffu, lit_v);
                         // the batch's Monte Carlo sum in a fixed lane order, whoever computes it
@@ -1302,6 +1324,7 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     if (nb > 256 || ns > 512) return VRC_ERR_UNSUPPORTED;
     if ((out->hit_prim != nullptr) != (out->hit_t != nullptr)) return VRC_ERR_INVALID;
     if (out->hit_prim && out->dbg_stride < nb * ns + 2) return VRC_ERR_INVALID;
+    if (out->dbg_lit && (!out->hit_prim || out->dbg_shells < 1)) return VRC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     int nt = s->tuning.threads ? s->tuning.threads : 256;
     int cb = s->tuning.chunk_bands;
@@ -1408,6 +1431,81 @@ extern "C" int vrc_compute_records_host(vrc_scene* s, const float* h_pos, int32_
     if (h_radius) VRC_CUDA_CHECK(cudaMemcpy(h_radius, v.radius, sizeof(float) * n, cudaMemcpyDeviceToHost));
     if (h_status) VRC_CUDA_CHECK(cudaMemcpy(h_status, v.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
     VRC_CUDA_CHECK(cudaDeviceSynchronize());
+    return VRC_OK;
+}
+
+// grow a scene-owned device staging buffer to hold `need` floats
+static int stage(float** buf, size_t* have, size_t need) {
+    if (*have >= need) return VRC_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc((void**)buf, need * sizeof(float)) != cudaSuccess) return VRC_ERR_OOM;
+    *have = need;
+    return VRC_OK;
+}
+
+extern "C" int vrc_cache_step_host(vrc_scene* s, vrc_grid** grid, const float* h_pos, int32_t n,
+                                   const vrc_record_params* p, const float* h_q, int32_t nq, float* h_L,
+                                   float* h_grad, float* h_hess, float* h_radius, int32_t* h_status, float* h_rgb,
+                                   int32_t* h_qstatus) {
+    if (!s || !grid || !p || n < 0 || nq < 0 || (n > 0 && !h_pos) || (nq > 0 && (!h_q || !h_rgb || !h_qstatus)))
+        return VRC_ERR_INVALID;
+    if (p->extrap_order != 1 && p->extrap_order != 2) return VRC_ERR_INVALID;
+    if (!s->step_made) {
+        for (int i = 0; i < 2; ++i) {
+            if (cudaStreamCreateWithFlags(&s->step_st[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&s->step_ev[i], cudaEventDisableTiming) != cudaSuccess)
+                return VRC_ERR_CUDA;
+        }
+        s->step_made = 1;
+    }
+    // staging (floats per record): pos 3, L 3, grad 9, hess 18, radius 1, status 1, pos copy 3;
+    // per query: point 3 in, rgb 3 + status 1 out
+    int rc;
+    if ((rc = stage(&s->h_stage_dev, &s->h_stage_floats, 38 * (size_t)(n > 0 ? n : 1))) ||
+        (rc = stage(&s->q_stage_dev, &s->q_stage_floats, 7 * (size_t)(nq > 0 ? nq : 1))))
+        return rc;
+    cudaStream_t main = s->step_st[0], side = s->step_st[1];
+    float* base = s->h_stage_dev;
+    float* d_pos = base;
+    vrc_records_view v = {};
+    v.L = base + 3 * (size_t)n;
+    v.grad = base + 6 * (size_t)n;
+    v.hess = base + 15 * (size_t)n;
+    v.radius = base + 33 * (size_t)n;
+    v.status = reinterpret_cast<int32_t*>(base + 34 * (size_t)n);
+    v.pos = base + 35 * (size_t)n;
+    float* d_q = s->q_stage_dev;
+    float* d_rgb = d_q + 3 * (size_t)nq;
+    int32_t* d_qst = reinterpret_cast<int32_t*>(d_rgb + 3 * (size_t)nq);
+    // the queries arrive on the side stream while the records are computed
+    if (nq > 0) VRC_CUDA_CHECK(cudaMemcpyAsync(d_q, h_q, 3 * sizeof(float) * nq, cudaMemcpyHostToDevice, side));
+    VRC_CUDA_CHECK(cudaEventRecord(s->step_ev[1], side));
+    if (n > 0) {
+        VRC_CUDA_CHECK(cudaMemcpyAsync(d_pos, h_pos, 3 * sizeof(float) * n, cudaMemcpyHostToDevice, main));
+        if ((rc = vrc_compute_records(s, d_pos, n, nullptr, p, &v, main)) != VRC_OK) return rc;
+        // the records leave on the side stream while the grid and the queries run
+        VRC_CUDA_CHECK(cudaEventRecord(s->step_ev[0], main));
+        VRC_CUDA_CHECK(cudaStreamWaitEvent(side, s->step_ev[0], 0));
+        if (h_L) VRC_CUDA_CHECK(cudaMemcpyAsync(h_L, v.L, 3 * sizeof(float) * n, cudaMemcpyDeviceToHost, side));
+        if (h_grad) VRC_CUDA_CHECK(cudaMemcpyAsync(h_grad, v.grad, 9 * sizeof(float) * n, cudaMemcpyDeviceToHost, side));
+        if (h_hess) VRC_CUDA_CHECK(cudaMemcpyAsync(h_hess, v.hess, 18 * sizeof(float) * n, cudaMemcpyDeviceToHost, side));
+        if (h_radius) VRC_CUDA_CHECK(cudaMemcpyAsync(h_radius, v.radius, sizeof(float) * n, cudaMemcpyDeviceToHost, side));
+        if (h_status)
+            VRC_CUDA_CHECK(cudaMemcpyAsync(h_status, v.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, side));
+    }
+    rc = *grid ? vrc_rebuild_record_grid(*grid, &v, n, p->extrap_order, 0, main)
+               : vrc_build_record_grid(&v, n, p->extrap_order, grid, main);
+    if (rc != VRC_OK) return rc;
+    if (nq > 0) {
+        VRC_CUDA_CHECK(cudaStreamWaitEvent(main, s->step_ev[1], 0));
+        if ((rc = vrc_query_inscatter(*grid, d_q, nq, d_rgb, d_qst, main)) != VRC_OK) return rc;
+        VRC_CUDA_CHECK(cudaMemcpyAsync(h_rgb, d_rgb, 3 * sizeof(float) * nq, cudaMemcpyDeviceToHost, main));
+        VRC_CUDA_CHECK(cudaMemcpyAsync(h_qstatus, d_qst, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, main));
+    }
+    VRC_CUDA_CHECK(cudaStreamSynchronize(main));
+    VRC_CUDA_CHECK(cudaStreamSynchronize(side));
     return VRC_OK;
 }
 

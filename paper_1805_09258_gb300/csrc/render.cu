@@ -309,6 +309,28 @@ __global__ void k_cell_levels(const float* pts, int n, int G, const int* cell_mi
     if (rep >= 0 && rep < n) level[i] = rep_level[rep];
 }
 
+__global__ void k_retire_level(int* level, int n, int lv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && level[i] == lv) level[i] = -1;
+}
+
+// The learned radius (shifted by logr_offset: the predictor's log radius at its training
+// tolerance plus (1/5) log of the ratio of tolerances, Eq. radiusAniso3D) is used only
+// where the coarse ray set's own Hessian puts the error of a record of that radius within
+// the tolerance: the error at R of Eq. radiusAniso3D, 4 pi |lambda| R^5 / (15 L), is at most
+// eps exactly when R <= the coarse record's radius (same L, lambda and eps).  Elsewhere
+// the prediction is replaced by logr_fallback (the candidate then starts with plain
+// placement); their count goes to *n_fallback.  radius_coarse NULL: the shift only.
+__global__ void k_mlp_fallback(const float* logr, float logr_offset, const float* radius_coarse, int n,
+                               float logr_fallback, float* logr_out, int* n_fallback) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float l = logr[i] + logr_offset;
+    bool ok = isfinite(l) && (!radius_coarse || __expf(l) <= radius_coarse[i]);
+    logr_out[i] = ok ? l : logr_fallback;
+    if (!ok) atomicAdd(n_fallback, 1);
+}
+
 __global__ void k_init_levels(const int* valid, int n, int start, int* level) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) level[i] = valid[i] ? start : -1;
@@ -415,6 +437,22 @@ extern "C" int vrc_update_coverage(const int32_t* d_count, int32_t n, int32_t* d
     if (n < 0 || (n > 0 && (!d_count || !d_level))) return VRC_ERR_INVALID;
     if (n == 0) return VRC_OK;
     k_cover<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_count, n, d_level);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_retire_level(int32_t* d_level, int32_t n, int32_t level, void* stream) {
+    if (n < 0 || (n > 0 && !d_level)) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    k_retire_level<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_level, n, level);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_mlp_fallback(const float* d_logr, int32_t n, float logr_offset, const float* d_radius_coarse,
+                                float logr_fallback, float* d_logr_out, int32_t* d_n_fallback, void* stream) {
+    if (n < 0 || (n > 0 && (!d_logr || !d_logr_out || !d_n_fallback))) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    k_mlp_fallback<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_logr, logr_offset, d_radius_coarse, n,
+                                                                    logr_fallback, d_logr_out, d_n_fallback);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 

@@ -550,6 +550,13 @@ extern "C" void vrc_destroy_scene(vrc_scene* s) {
     cudaFree(s->d_pre_ray);
     cudaFree(s->d_pre_Lo);
     cudaFree(s->h_stage_dev);
+    cudaFree(s->q_stage_dev);
+    if (s->step_made) {
+        for (int i = 0; i < 2; ++i) {
+            cudaStreamDestroy(s->step_st[i]);
+            cudaEventDestroy(s->step_ev[i]);
+        }
+    }
     for (int l = 0; l < VRC_MAX_LIGHTS; ++l) {
         cudaFree(s->d_lb_cell[l]);
         cudaFree(s->d_lb_ent[l]);

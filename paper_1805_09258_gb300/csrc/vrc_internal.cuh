@@ -71,6 +71,13 @@ struct vrc_scene {
     // device staging for vrc_compute_records_host (grown on demand)
     float* h_stage_dev;
     size_t h_stage_floats;
+    // vrc_cache_step_host: query staging (grown on demand), a side stream for the copies
+    // that overlap the kernels, and the two events that order it against the main stream
+    float* q_stage_dev;
+    size_t q_stage_floats;
+    cudaStream_t step_st[2];
+    cudaEvent_t step_ev[2];
+    int step_made;
 };
 
 // Record grid (query.cu builds it; the renderer reads it): compact record rows and a

@@ -135,6 +135,32 @@ def test_host_buffer_entry_point_matches_device_entry_point(vrc):
         assert np.array_equal(h[k], d[k]), k
 
 
+def test_whole_step_from_host_buffers_matches_device_calls(vrc):
+    """vrc_cache_step_host (host positions and points in; records and query answers out,
+    copies inside the call) gives, bit for bit, what the device calls give: records as
+    vrc_compute_records, answers as vrc_build_record_grid + vrc_query_inscatter; also on a
+    second call, which rebuilds the grid in place."""
+    w = W.config2()
+    step = vrc.HostStep(vrc.Scene.from_workload(w.scene), w.params)
+    s = vrc.Scene.from_workload(w.scene)
+    for seed in (5, 6):
+        pos = w.positions(500, seed=seed)
+        q = w.queries(40000, seed=seed)
+        out = {"L": np.zeros((500, 3), np.float32), "grad": np.zeros((500, 9), np.float32),
+               "hess": np.zeros((500, 18), np.float32), "radius": np.zeros(500, np.float32),
+               "status": np.zeros(500, np.int32), "rgb": np.zeros((40000, 3), np.float32),
+               "qstatus": np.zeros(40000, np.int32)}
+        step(pos, q, out)
+        d = vrc.compute_records(s, torch.from_numpy(pos).cuda(), w.params)
+        rgb, cnt = vrc.query_inscatter(vrc.Grid(d, extrap_order=w.params.extrap_order), torch.from_numpy(q).cuda())
+        torch.cuda.synchronize()
+        d = to_np(d)
+        for k in ("L", "grad", "hess", "radius", "status"):
+            assert np.array_equal(out[k], d[k]), (seed, k)
+        assert np.array_equal(out["rgb"], rgb.cpu().numpy()) and np.array_equal(out["qstatus"], cnt.cpu().numpy())
+        assert (out["qstatus"] > 0).mean() > 0.5
+
+
 def test_hit_ids_agree_except_near_edges(vrc):
     """Primary hit primitive ids agree on >= 99.99% of rays; a mismatch is allowed only
     where the oracle's ray passes within 1e-5 of a triangle edge (or meets two
