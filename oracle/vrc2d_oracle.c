@@ -362,8 +362,11 @@ static void cell2(v2 x, const v2 y[2], const double t[2], const double* Lo[2], c
     }
 }
 
-/* x_eval: the point at which the frozen cells are evaluated (x itself for a record) */
-static void record2(const o2_scene* s, const o2_params* p, v2 x, v2 x_eval, int64_t rec, double* out) {
+/* x_eval: the point at which the frozen cells are evaluated (x itself for a record).
+ * replay (nullable): a primary hit segment per ray (-1 = none) used instead of the
+ * oracle's own closest hit (replay mode: the decision is the given one, the rest FP64). */
+static void record2(const o2_scene* s, const o2_params* p, v2 x, v2 x_eval, int64_t rec, const int32_t* replay,
+                    double* out) {
     const int N = p->n_dirs;
     const double sig_t = (double)s->sigma_s + (double)s->sigma_a;
     memset(out, 0, sizeof(double) * O2_STRIDE);
@@ -388,6 +391,15 @@ static void record2(const o2_scene* s, const o2_params* p, v2 x, v2 x_eval, int6
             id = 0;
         } else {
             id = closest2(s, x, dir[j], &t, &ne);
+            if (replay && replay[j] != id && replay[j] >= -1 && replay[j] < s->n_segs) {
+                id = replay[j];
+                if (id >= 0) {        /* the given segment's line, its endpoints not tested */
+                    v2 e = sub2(seg_b(s, id), seg_a(s, id)), w = sub2(seg_a(s, id), x);
+                    double den = crs2(dir[j], e);
+                    if (den != 0.0) t = crs2(w, e) / den;
+                }
+            }
+            if (replay) ne = 1e300;
             if (id >= 0) surface_Lo(s, id, add2(x, scl2(dir[j], t)), dir[j], &Ls[3 * j], &dLs[3 * j]);
             else t = square_exit(x, dir[j]);
         }
@@ -489,11 +501,13 @@ static void record2(const o2_scene* s, const o2_params* p, v2 x, v2 x_eval, int6
 
 int o2_stride(void) { return O2_STRIDE; }
 
-int o2_records(const o2_scene* s, const o2_params* p, const float* pos, const int64_t* rec_ids, int n, double* out) {
+/* n records; replay (nullable) gives replay_stride primary hit segment ids per record */
+int o2_records(const o2_scene* s, const o2_params* p, const float* pos, const int64_t* rec_ids, int n, double* out,
+               const int32_t* replay, int replay_stride) {
     for (int i = 0; i < n; ++i) {
         v2 x = mk2(pos[2 * i], pos[2 * i + 1]);
         int64_t rid = rec_ids ? rec_ids[i] : p->rec_base + i;
-        record2(s, p, x, x, rid, out + (size_t)i * O2_STRIDE);
+        record2(s, p, x, x, rid, replay ? replay + (size_t)i * replay_stride : NULL, out + (size_t)i * O2_STRIDE);
     }
     return 0;
 }
@@ -502,7 +516,7 @@ int o2_records(const o2_scene* s, const o2_params* p, const float* pos, const in
  * cells evaluated at x_eval (for frozen-vertex finite differences) */
 int o2_frozen_eval(const o2_scene* s, const o2_params* p, const float* x0, int64_t rec, const double* x_eval,
                    double* out) {
-    record2(s, p, mk2(x0[0], x0[1]), mk2(x_eval[0], x_eval[1]), rec, out);
+    record2(s, p, mk2(x0[0], x0[1]), mk2(x_eval[0], x_eval[1]), rec, NULL, out);
     return 0;
 }
 

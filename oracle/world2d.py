@@ -51,7 +51,7 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(build())
         P = C.c_void_p
-        _lib.o2_records.argtypes = [P, P, P, P, C.c_int, P]
+        _lib.o2_records.argtypes = [P, P, P, P, C.c_int, P, P, C.c_int]
         _lib.o2_frozen_eval.argtypes = [P, P, P, C.c_int64, P, P]
         _lib.o2_segment_angle.argtypes = [P, P, P, P]
         _lib.o2_transmittance.argtypes = [P, P, C.c_double, P]
@@ -117,15 +117,18 @@ def make_params(rp) -> _Params:
     return p
 
 
-def records(oscene: OracleScene2, rp, pos, rec_ids=None) -> dict:
+def records(oscene: OracleScene2, rp, pos, rec_ids=None, replay_hits=None) -> dict:
     """2D records at pos [n, 2] (float32).  Returns a dict of arrays keyed as SLOTS:
-    grad [n, 3, 2], hess [n, 3, 3] (xx, xy, yy per channel)."""
+    grad [n, 3, 2], hess [n, 3, 3] (xx, xy, yy per channel).  replay_hits (int [n, >= N]):
+    a primary hit segment id per ray (-1 = none) used instead of the oracle's own closest
+    hit (replay mode); prim_near then counts no ray."""
     pos = _f32(pos).reshape(-1, 2)
     n = pos.shape[0]
     ids = None if rec_ids is None else np.ascontiguousarray(rec_ids, dtype=np.int64)
+    rh = None if replay_hits is None else np.ascontiguousarray(replay_hits, dtype=np.int32).reshape(n, -1)
     out = np.zeros((n, STRIDE))
     p = make_params(rp)
-    lib().o2_records(oscene.ptr, C.byref(p), _p(pos), _p(ids), n, _p(out))
+    lib().o2_records(oscene.ptr, C.byref(p), _p(pos), _p(ids), n, _p(out), _p(rh), 0 if rh is None else rh.shape[1])
     res = {}
     for k, (o, w) in SLOTS.items():
         res[k] = out[:, o] if w == 1 else out[:, o:o + w]

@@ -277,6 +277,10 @@ __global__ void __launch_bounds__(NT2) k_records2d(Scene2View sc, Rec2Args a) {
             } else {
                 t = square_exit(x, d);
             }
+            if (a.out.hit_prim) {                    // debug: the primary hit decisions
+                a.out.hit_prim[(size_t)rec * a.out.dbg_stride + j] = prim;
+                a.out.hit_t[(size_t)rec * a.out.dbg_stride + j] = t;
+            }
             ray[j] = make_float4(d.x, d.y, t, 0.f);
             Lr[j] = Lo.x;
             Lg[j] = Lo.y;
@@ -530,6 +534,7 @@ extern "C" int vrc2d_compute_records(vrc2d_scene* s, const float* d_pos, int32_t
         !(p->r_max >= p->r_min) || p->parts < 0 || p->parts > 2)
         return VRC_ERR_INVALID;
     if (N > 4096) return VRC_ERR_UNSUPPORTED;
+    if (out->hit_prim && (!out->hit_t || out->dbg_stride < N)) return VRC_ERR_INVALID;
     size_t smem = rec2_smem(N);
     cudaStream_t st = (cudaStream_t)stream;
     Scene2View sv;

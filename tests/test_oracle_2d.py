@@ -220,3 +220,27 @@ def test_trace_matches_numpy_brute_force():
         assert ids[i] == best
         if best >= 0:
             assert t[i] == pytest.approx(bt, rel=1e-12)
+
+
+def test_replaying_own_hits_changes_nothing():
+    """Replay mode of the 2D oracle: given its own primary hit segments, a record is
+    unchanged; given a miss for one ray that hits, only that ray's terms change (its
+    surface radiance leaves the Monte Carlo sum, its shells run to the square's edge)."""
+    w = flat.flat_small()
+    pos = w.positions(16)
+    osc = O2.OracleScene2(w.scene)
+    r = O2.records(osc, w.params, pos)
+    N = w.params.n_bins
+    dirs = np.stack([O2.ray_directions(w.params, i) for i in range(pos.shape[0])])
+    hits = np.stack([O2.trace(osc, np.repeat(pos[i:i + 1].astype(np.float64), N, 0), dirs[i])[0]
+                     for i in range(pos.shape[0])]).astype(np.int32)
+    rr = O2.records(osc, w.params, pos, replay_hits=hits)
+    for k in ("L", "grad", "hess", "radius"):
+        assert np.array_equal(rr[k], r[k]), k
+    assert np.all(rr["prim_near"] == 0)
+    h2 = hits.copy()
+    j = int(np.flatnonzero(hits[0] >= 0)[0])
+    h2[0, j] = -1
+    r2 = O2.records(osc, w.params, pos[:1], replay_hits=h2[:1])
+    assert not np.array_equal(r2["L_ss"][0], r["L_ss"][0])
+    assert np.all(r2["L_ss"][0] < r["L_ss"][0] + 1e-15)
