@@ -60,8 +60,23 @@ def test_synthetic_table_parity(vrc, order):
     rgb, cnt, _ = gpu_query(vrc, tab, q, order)
     ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=order)
     check_query(rgb, cnt, ref, rc, near)
-    assert np.allclose(rgb[20000:20050], tab["L"][:50] * 0 + rgb[20000:20050])   # finite at centres
     assert cnt.max() > 1 and (cnt == 0).any()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_exact_at_the_centre_of_a_lone_record(vrc, order):
+    """Eq. radianceTaylor at a record's centre, where no other record reaches: the weight is
+    w(1) = 1 and the Taylor terms vanish, so the answer is L_k itself, bit for bit (the
+    oracle's pin of the same fact is in test_oracle_pins)."""
+    g = (np.arange(5) + 0.5) / 5.0                     # a 5 x 5 x 5 lattice, spacing 0.2
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    n = pos.shape[0]
+    tab = synthetic_table(n, seed=31)
+    tab["pos"] = pos.astype(np.float32)
+    tab["radius"] = np.random.default_rng(32).uniform(0.02, 0.099, n).astype(np.float32)   # < half the spacing
+    rgb, cnt, _ = gpu_query(vrc, tab, tab["pos"], order)
+    assert np.all(cnt == 1)
+    assert np.array_equal(rgb, tab["L"])
 
 
 def test_sizes_ragged_and_degenerate(vrc):
@@ -113,6 +128,25 @@ def test_records_then_queries_end_to_end(vrc):
     assert np.array_equal(cnt[~sensitive], qc[~sensitive])
     both = (~sensitive) & (qc > 0)
     assert np.all(np.abs(rgb[both] - qo[both]) <= 2e-3 * np.abs(qo[both]).max(axis=1, keepdims=True) + 1e-6)
+
+
+def test_full_size_query_parity(vrc):
+    """The benchmark's query call: the 4,096 records of the mid workload (the oracle's, as
+    a table common to both sides) in the record grid, all 1,048,576 queries in one launch;
+    131,072 of them compared element by element with the oracle's brute force."""
+    w = W.config2()
+    pos = w.positions()
+    ref = O.records(O.OracleScene(w.scene), w.params, pos)
+    tab = {"pos": pos, "radius": ref["radius"], "L": ref["L"], "grad": ref["grad"], "hess": ref["hess"]}
+    tab = {k: np.ascontiguousarray(v, dtype=np.float32) for k, v in tab.items()}
+    q = w.queries()
+    assert q.shape[0] == 1 << 20
+    rgb, cnt, _ = gpu_query(vrc, tab, q, w.params.extrap_order)
+    sel = np.random.default_rng(41).choice(q.shape[0], 131072, replace=False)
+    oref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], tab["hess"], q[sel],
+                             order=w.params.extrap_order)
+    check_query(rgb[sel], cnt[sel], oref, rc, near)
+    assert (rc > 0).mean() > 0.5 and rc.max() > 10
 
 
 def test_rebuild_in_place_matches_a_new_grid(vrc):
