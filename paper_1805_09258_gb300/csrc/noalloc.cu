@@ -9,6 +9,8 @@
 // budget.  vrc_query_inscatter_noalloc answers the same queries from the caller's
 // record buffers with all of its working memory in one file-scope device array of
 // fixed size, so it never calls cudaMalloc, cudaFree or an allocating library routine.
+// It serves sphere records (the grids vrc_build_record_grid builds); the ellipsoid fields
+// of the records (radii, axes) are not read.
 //
 // The working memory (VRC_NOALLOC_SCRATCH_INTS 32-bit words, 4 MiB) is a coarse
 // 16 x 16 x 16 grid over the unit cube: per-cell counts, start offsets and the lists
@@ -115,16 +117,62 @@ __global__ void k_na_scan(int* s) {
     }
 }
 
-__global__ void k_na_sort(int* s) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= NA_CELLS || s[0]) return;
+// One block per cell puts the cell's list in ascending record order, so the queries sum
+// their candidates in a fixed order.  The ids of a cell are distinct and below n <= 65,536:
+// short lists are rank-sorted in shared memory; longer ones set one bit per id in a shared
+// bitmap of n bits (8 KiB at most) and write the set bits back in order, O(len + n / 32).
+#define NA_SORT_THREADS 256
+#define NA_RANK_CAP 512
+__global__ void __launch_bounds__(NA_SORT_THREADS) k_na_sort(int* s, int n) {
+    __shared__ unsigned bits[VRC_NOALLOC_MAX_RECORDS / 32];
+    __shared__ int part[NA_SORT_THREADS];
+    const int cell = blockIdx.x, tid = threadIdx.x;
+    if (s[0]) return;                            // overflowed: no lists
     const int* starts = s + NA_HEADER + NA_CELLS;
     int* list = s + NA_LIST_OFFSET;
-    int b = starts[cell], e = starts[cell + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = list[i], j = i - 1;
-        while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
-        list[j + 1] = v;
+    const int b = starts[cell], len = starts[cell + 1] - b;
+    if (len <= 1) return;
+    if (len <= NA_RANK_CAP) {
+        int* buf = reinterpret_cast<int*>(bits);
+        for (int i = tid; i < len; i += NA_SORT_THREADS) buf[i] = list[b + i];
+        __syncthreads();
+        for (int i = tid; i < len; i += NA_SORT_THREADS) {
+            const int v = buf[i];
+            int r = 0;
+            for (int j = 0; j < len; ++j) r += buf[j] < v;
+            list[b + r] = v;
+        }
+        return;
+    }
+    const int words = (n + 31) >> 5;
+    for (int w = tid; w < words; w += NA_SORT_THREADS) bits[w] = 0u;
+    __syncthreads();
+    for (int i = tid; i < len; i += NA_SORT_THREADS) {
+        const int id = list[b + i];
+        atomicOr(&bits[id >> 5], 1u << (id & 31));
+    }
+    __syncthreads();
+    // each thread owns a contiguous run of words; an exclusive scan of their bit counts
+    // gives its first output slot
+    const int per = (words + NA_SORT_THREADS - 1) / NA_SORT_THREADS;
+    const int w0 = min(tid * per, words), w1 = min(w0 + per, words);
+    int cnt = 0;
+    for (int w = w0; w < w1; ++w) cnt += __popc(bits[w]);
+    part[tid] = cnt;
+    __syncthreads();
+    for (int off = 1; off < NA_SORT_THREADS; off <<= 1) {
+        const int t = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += t;
+        __syncthreads();
+    }
+    int o = b + part[tid] - cnt;
+    for (int w = w0; w < w1; ++w) {
+        unsigned m = bits[w];
+        while (m) {
+            list[o++] = (w << 5) + __ffs(m) - 1;
+            m &= m - 1u;
+        }
     }
 }
 
@@ -205,7 +253,7 @@ extern "C" int vrc_query_inscatter_noalloc(const vrc_records_view* recs, int32_t
         k_na_insert<false><<<nb, 256, 0, st>>>(recs->pos, recs->radius, n, s);
         k_na_scan<<<1, 1024, 0, st>>>(s);
         k_na_insert<true><<<nb, 256, 0, st>>>(recs->pos, recs->radius, n, s);
-        k_na_sort<<<NA_CELLS / 128, 128, 0, st>>>(s);
+        k_na_sort<<<NA_CELLS, NA_SORT_THREADS, 0, st>>>(s, n);
     } else {
         k_na_scan<<<1, 1024, 0, st>>>(s);
     }
