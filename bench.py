@@ -480,6 +480,19 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                                               replay_t=gpu_dbg["hit_t"], replay_lit=gpu_dbg["dbg_lit"])
                     own = oracle.records(osc, w.params, pos, track_margins=1)
                     line["precision_vs_oracle"]["decisions"] = decision_report(gpu_dbg, replayed, own)
+        if not args.no_learned:
+            # learned vs plain record placement at equal error (after the timed region)
+            try:
+                c = learned_comparison()
+                line["learned_vs_plain"] = {
+                    "summary": c["summary"], "speedups_at_equal_error": c["speedups_at_equal_error"],
+                    "training": c["training"], "workload": c["workload"],
+                    "runs": {k: {"records": v["records"], "placement_ms": v["placement_ms"],
+                                 "mean_rel_err": v["mean_rel_err"], "fallback_sites": v["fallback_sites"],
+                                 "predicted_sites": v["predicted_sites"]} for k, v in c["runs"].items()},
+                    "reference_noise_floor": c["reference_noise_floor"]}
+            except Exception as ex:          # reported, not fatal to the line
+                line["learned_vs_plain"] = {"error": f"{type(ex).__name__}: {ex}"}
         print(json.dumps(line), flush=True)
     return line
 
@@ -639,33 +652,49 @@ def run_mlp(args):
     print(json.dumps(line), flush=True)
 
 
-def run_learned(args):
-    """Extra measurement (not the default line): learned vs plain placement on the learned
-    workload (mid-style scenes).  The predictor is trained on records of 8 scenes (seeds
-    1..8); on a held-out scene (seed 41) 60,000 candidate points are covered by plain and by
-    learned placement at four tolerances (1, 1/10, 1/100 and 1/1000 of the workload's); the
-    error is the cache's per-point relative luminance error at 619 held-out candidates
-    against a 64x128-ray record there (mean,
-    median, 90th percentile; the RMSE over the mean, which a few bright points near the light
-    dominate, is reported too, and so is the reference's own noise), and the learned path's
-    placement time is compared with the plain path's at equal mean error (log-log
-    interpolation between the two nearest plain tolerances)."""
+def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 3000) -> dict:
+    """Learned vs plain record placement at equal error (the learned radius predictor is not
+    in the paper).  Training set: n_scenes seeded mid-style scenes x per_scene positions
+    (16 x 65,536 = 1,048,576 records by default), full 32x64 records by the plain path give
+    the targets log R, coarse 8x16 ray sets the features; rows are shuffled across scenes
+    and split 80/10/10 (train / validation / test; the held-out errors are reported).
+    Placement runs on a held-out scene (seed 41): 60,000 candidate points covered by plain
+    waves, learned waves and learned one-shot placement (every predicted level's sites in
+    one batched launch, then plain repair waves), each at 1, 1/10, 1/100 and 1/1000 of the
+    workload's tolerance, with the predictor's radius carried to each tolerance and checked
+    against the coarse record (vrc_mlp_fallback).  Error: per-point relative luminance
+    error at 619 held-out candidates against a 64x128-ray record there (mean, median, 90th
+    percentile, relative RMSE; the reference's own noise is reported too).  A learned run is
+    compared with the plain path's placement time and record count at its own mean error
+    (log-log interpolation between the two nearest plain tolerances)."""
     import torch
     import oracle.mlp as M
     import paper_1805_09258_gb300 as vrc
-    from paper_1805_09258_gb300 import build as vbuild, learned, placement
-    vbuild.build()
+    from paper_1805_09258_gb300 import learned, placement
     coarse = W.RecordParams(n_bands=8, n_bins=16, seed=W.configs.SEED_JITTER + 1000)
     t0 = time.perf_counter()
-    ex = learned.ExampleSet(8 * 8192)
-    for seed in range(1, 9):
+    ex = learned.ExampleSet(n_scenes * per_scene)
+    for seed in range(1, n_scenes + 1):
         w = W.config4(scene_seed=seed)
-        ex.add(vrc.Scene.from_workload(w.scene), w.positions(8192, seed=100 + seed), w.params, coarse)
+        ex.add(vrc.Scene.from_workload(w.scene), w.positions(per_scene, seed=100 + seed), w.params, coarse)
     F, T = ex.view(shuffle=True)
+    n = F.shape[0]
+    n_tr, n_va = int(0.8 * n), int(0.1 * n)
     mlp = vrc.MLP(M.init_params(21))
-    learned.train(mlp, F, T, steps=1500, batch=4096, lr=2e-3)
+    learned.train(mlp, F[:n_tr], T[:n_tr], steps=steps, batch=4096, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+
+    def held_out(lo, hi):
+        pred = mlp.predict(F[lo:hi].contiguous())
+        tt = T[lo:hi]
+        mse = float(((pred - tt) ** 2).mean())
+        return {"rows": hi - lo, "mse_log_r": mse, "r2": 1.0 - mse / float(tt.var())}
+
+    fit = {"train_rows": n_tr, "validation": held_out(n_tr, n_tr + n_va), "test": held_out(n_tr + n_va, n)}
+    del ex, F, T
+    torch.cuda.empty_cache()
+
     w = W.config4(scene_seed=41)
     s = vrc.Scene.from_workload(w.scene)
     cand = torch.from_numpy(w.positions(60000, seed=441)).cuda()
@@ -674,7 +703,6 @@ def run_learned(args):
     ref = vrc.compute_records(s, q, rp_ref, full=False)["L"].cpu().numpy().astype(np.float64)
     ref2 = vrc.compute_records(s, q, W.configs.replace(rp_ref, seed=W.configs.SEED_JITTER + 8),
                                full=False)["L"].cpu().numpy().astype(np.float64)
-
     Y = np.array([0.2126, 0.7152, 0.0722])
     Yref = ref @ Y
     floor = 1e-2 * np.mean(np.abs(Yref))
@@ -686,12 +714,17 @@ def run_learned(args):
     def rel_rmse(L):
         return float(np.sqrt(np.mean((L - ref) ** 2)) / np.mean(np.abs(ref)))
 
+    eps0 = w.params.eps
+    variants = (("plain", {}),
+                ("learned", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0)),
+                ("learned_one_shot", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
+                                          one_shot=True)))
     res = {}
     # the tolerance bounds the error integrated over a record's ball (Eq. radiusAniso3D), so
     # the per-point error falls slowly with it (the radius goes as its fifth root)
-    for eps in (w.params.eps, w.params.eps / 10, w.params.eps / 100, w.params.eps / 1000):
+    for eps in (eps0, eps0 / 10, eps0 / 100, eps0 / 1000):
         rp = W.configs.replace(w.params, eps=eps)
-        for name, kw in (("plain", {}), ("learned", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5))):
+        for name, kw in variants:
             placement.place(s, rp, cand, **kw)                     # warm-up
             torch.cuda.synchronize()
             r = placement.place(s, rp, cand, **kw)
@@ -699,14 +732,15 @@ def run_learned(args):
             L = rgb.cpu().numpy().astype(np.float64)
             e = rel_err(L)
             res[f"{name}_eps{eps:g}"] = {"records": r.n_records, "placement_ms": r.seconds * 1e3,
-                                         "mean_rel_err": float(e.mean()), "median_rel_err": float(np.median(e)),
-                                         "p90_rel_err": float(np.quantile(e, 0.9)), "rel_rmse": rel_rmse(L),
-                                         "uncovered": int((cnt == 0).sum())}
+                                         "waves": len(r.waves), "mean_rel_err": float(e.mean()),
+                                         "median_rel_err": float(np.median(e)), "p90_rel_err": float(np.quantile(e, 0.9)),
+                                         "rel_rmse": rel_rmse(L), "uncovered": int((cnt == 0).sum()),
+                                         "predicted_sites": r.predicted_sites, "fallback_sites": r.fallback_sites}
     plain = sorted((v["mean_rel_err"], v["placement_ms"], v["records"]) for k, v in res.items()
                    if k.startswith("plain"))
     equal = {}
     for k, v in res.items():
-        if not k.startswith("learned"):
+        if k.startswith("plain"):
             continue
         e = v["mean_rel_err"]
         lo = [p for p in plain if p[0] <= e]
@@ -721,15 +755,29 @@ def run_learned(args):
                         "learned_records": v["records"]}
         else:
             equal[k] = {"mean_rel_err": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
-    base = res[f"learned_eps{w.params.eps:g}"]
-    line = {"metric": METRIC, "value": cand.shape[0] / (base["placement_ms"] * 1e-3),
-            "unit": "candidate points covered/s (learned placement)", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "higher_is_better": True, "dtype": "f32 records, bf16 predictor", "data": "synthetic",
-            "config": {"workload": "learned: mid-style scene (seed 41), 60,000 candidates, records 32x64, "
-                                   "coarse features 8x16"},
-            "runs": res, "equal_error": equal, "mlp_training_s": train_s,
+    sp = {k: v["speedup"] for k, v in equal.items() if "speedup" in v}
+    best = max(sp, key=sp.get) if sp else None
+    verdict = ("no learned run falls inside the plain runs' error range" if best is None else
+               (f"learned faster than plain at equal error: best {best} {sp[best]:.2f}x" if sp[best] > 1.0 else
+                f"learned slower than plain at equal error: best {best} {sp[best]:.2f}x"))
+    return {"workload": "learned: predictor trained on 16 mid-style scenes (1,048,576 records), placement on a "
+                        "held-out scene (seed 41), 60,000 candidates, records 32x64, coarse features 8x16",
+            "training": dict(fit, seconds=train_s, steps=steps), "runs": res, "equal_error": equal,
+            "summary": verdict, "speedups_at_equal_error": sp,
             "reference_noise_floor": {"mean_rel_err": float(rel_err(ref2).mean()),
                                       "rel_rmse": float(np.sqrt(np.mean((ref2 - ref) ** 2)) / np.mean(np.abs(ref)))}}
+
+
+def run_learned(args):
+    """Extra measurement: the learned-vs-plain comparison (learned_comparison) as its own line."""
+    from paper_1805_09258_gb300 import build as vbuild
+    vbuild.build()
+    cmp_ = learned_comparison()
+    base = cmp_["runs"][f"learned_one_shot_eps{W.config4().params.eps:g}"]
+    line = {"metric": METRIC, "value": 60000 / (base["placement_ms"] * 1e-3),
+            "unit": "candidate points covered/s (learned one-shot placement)", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "dtype": "f32 records, bf16 predictor", "data": "synthetic",
+            "config": {"workload": cmp_["workload"]}, **{k: v for k, v in cmp_.items() if k != "workload"}}
     print(json.dumps(line), flush=True)
 
 
@@ -795,6 +843,29 @@ def run_render(args, w):
         return float(np.sqrt(np.mean((img - ref) ** 2)) / np.mean(np.abs(ref)))
 
     floor = rel_rmse(ref2)
+    # the FP64 reference: the frame's central 64 x 64 pixels with a full oracle record at
+    # every march point (oracle/render.py; computed once into the oracle's cache directory)
+    import oracle.render as orender
+    crop_path = orender.render_crop_path(64)
+    fp64 = None
+    if os.path.exists(crop_path):
+        fp64 = orender.central_crop(64)
+        cx0, cy0, cs = int(fp64["x0"]), int(fp64["y0"]), int(fp64["w"])
+        fp_img = fp64["img"].reshape(-1, 3)
+        # the same pixels from a full GPU record at every march point (same record ids, so
+        # the same ray sets): the uncached path against the oracle, up to FP32 rounding
+        cpts, _ = vrc.march_points(scene, cam, cx0, cy0, cs, cs, 1, steps)
+        cfull = vrc.compute_records(scene, cpts, rp, full=False)
+        gimg = vrc.composite(scene, cam, cx0, cy0, cs, cs, steps, cfull["L"]).cpu().numpy().astype(np.float64)
+        uncached = float(np.sqrt(np.mean((gimg - fp_img) ** 2)) / np.mean(np.abs(fp_img)))
+        del cpts, cfull
+
+    def rel_rmse_fp64(im):
+        if fp64 is None:
+            return None
+        c = im[cy0:cy0 + cs, cx0:cx0 + cs].reshape(-1, 3).astype(np.float64)
+        return float(np.sqrt(np.mean((c - fp_img) ** 2)) / np.mean(np.abs(fp_img)))
+
     # FP64 oracle spot check of reference records
     pn = pts_all[5].cpu().numpy()
     idx = np.arange(0, pn.shape[0], pn.shape[0] // 8)[:8]
@@ -812,23 +883,25 @@ def run_render(args, w):
     res = {}
     for name, net, eps, aniso, split in runs:
         rpe = W.configs.replace(rp, eps=eps)
-        kw = dict(steps=steps, stride=8, mlp=net, coarse_params=coarse, aniso=aniso, split=split)
+        kw = dict(steps=steps, stride=8, mlp=net, coarse_params=coarse, aniso=aniso, split=split, eps_train=rp.eps)
         render_frame(scene, cam, rpe, **kw)     # warm-up
         fr = render_frame(scene, cam, rpe, **kw)
         im = fr.image.cpu().numpy().reshape(Hd, Wd, 3)
         img = np.concatenate([im[y0:y0 + cw, x0:x0 + cw].reshape(-1, 3) for (x0, y0) in crops])
         res[name] = {"frame_ms": fr.seconds * 1e3, "placement_ms": fr.placement_s * 1e3, "records": fr.n_records,
-                     "rel_rmse": rel_rmse(img),
+                     "rel_rmse": rel_rmse(img), "rel_rmse_fp64_crop": rel_rmse_fp64(im),
                      "eps": eps, "passes": len(fr.passes), "misses_repaired": fr.misses,
                      "records_ss_ms": None if fr.placement2 is None else [fr.placement.n_records,
                                                                           fr.placement2.n_records]}
-    # equal-error comparison: plain frame time interpolated at each learned run's error
-    plain = sorted((v["rel_rmse"], v["frame_ms"], v["records"]) for k, v in res.items() if k.startswith("plain_eps"))
+    # equal-error comparison: plain frame time interpolated at each other run's error (against
+    # the FP64 crop when it is there, else the 16-crop reference)
+    key = "rel_rmse_fp64_crop" if fp64 is not None else "rel_rmse"
+    plain = sorted((v[key], v["frame_ms"], v["records"]) for k, v in res.items() if k.startswith("plain_eps"))
     equal = {}
     for k, v in res.items():
-        if not k.startswith("learned_eps"):
+        if k.startswith("plain_eps"):
             continue
-        e = v["rel_rmse"]
+        e = v[key]
         lo = [p for p in plain if p[0] <= e]
         hi = [p for p in plain if p[0] >= e]
         if lo and hi:
@@ -839,9 +912,9 @@ def run_render(args, w):
                 f_ = (math.log(e) - math.log(a[0])) / (math.log(b[0]) - math.log(a[0]))
                 t = math.exp(math.log(a[1]) + f_ * (math.log(b[1]) - math.log(a[1])))
                 n = math.exp(math.log(a[2]) + f_ * (math.log(b[2]) - math.log(a[2])))
-            equal[k] = {"rel_rmse": e, "plain_frame_ms_at_equal_error": t, "learned_frame_ms": v["frame_ms"],
+            equal[k] = {key: e, "plain_frame_ms_at_equal_error": t, "frame_ms": v["frame_ms"],
                         "speedup": t / v["frame_ms"], "plain_records_at_equal_error": n,
-                        "learned_records": v["records"]}
+                        "records": v["records"]}
         else:
             equal[k] = {"mean_rel_err": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
     n_q = Wd * Hd * steps
@@ -855,6 +928,11 @@ def run_render(args, w):
             "mlp_training_s": train_s,
             "reference": "64x128-ray record at every march point of 16 crops of 16x16 pixels (5x4 lattice, "
                          "crops near the light's image left out)",
+            "equal_error_measure": key,
+            "fp64_crop": None if fp64 is None else
+            {"pixels": f"central {cs}x{cs} (x0 {cx0}, y0 {cy0}), {steps} march points each",
+             "records": int(cs * cs * steps), "oracle_seconds": float(fp64.get("seconds", 0.0)),
+             "uncached_gpu_rel_rmse": uncached},
             "light_pixel": [lx, ly],
             "reference_noise_floor_rel_rmse": floor,
             "oracle_spot_check_max_err_over_tol": spot}
@@ -869,6 +947,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain placement comparison")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
     ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat", "mlp", "learned"],

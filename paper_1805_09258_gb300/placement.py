@@ -13,7 +13,15 @@ Plain placement starts every candidate at the coarsest level.  Learned placement
 predicts each candidate's radius from its coarse ray set (vrc_coarse_features,
 vrc_mlp_predict) and lets it join only at the wave whose cell matches that radius
 (vrc_levels_from_radius): regions of small radius skip the coarse waves, whose records
-would cover almost nothing there.
+would cover almost nothing there.  A prediction made at the training tolerance is carried
+to the placement's tolerance (R goes as eps^(1/5), Eq. radiusAniso3D), and it is kept only
+where a record of the coarse ray set itself puts the error at the predicted radius within
+the tolerance (vrc_mlp_fallback); elsewhere the candidate falls back to plain placement.
+
+One-shot (batched) learned placement selects the sites of every predicted level at once
+(level by level on a copy of the pool, vrc_retire_level) and computes all their records
+in one persistent launch, with one grid build and one coverage query; the few candidates
+left uncovered then go through the plain waves at their predicted levels.
 
 This module only sequences library calls; all work runs in libvrc's kernels.
 """
@@ -22,8 +30,12 @@ from __future__ import annotations
 import time
 from dataclasses import dataclass, field
 
+import dataclasses
+import math
+
 from . import (MLP, Grid, Scene, alloc_records, coarse_features, compute_records, init_levels, levels_by_cell,
-               levels_from_radius, query_inscatter, select_sites, update_coverage, _torch)
+               levels_from_radius, mlp_fallback, query_inscatter, retire_level, select_sites, update_coverage,
+               _torch)
 
 
 @dataclass
@@ -34,16 +46,22 @@ class PlacementResult:
     records: dict = None
     grid: Grid = None
     uncovered_after_waves: int = 0
+    predicted_sites: int = 0
+    fallback_sites: int = 0
 
 
 def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, mlp: MLP = None,
           coarse_params=None, cell_over_radius: float = 1.0, capacity: int = None, valid=None,
-          base: PlacementResult = None, predict_level: int = 5, aniso: bool = False) -> PlacementResult:
+          base: PlacementResult = None, predict_level: int = 5, aniso: bool = False, eps_train: float = None,
+          fallback: bool = True, one_shot: bool = False) -> PlacementResult:
     """Place records until every candidate point `cand` [n,3] (CUDA float32) is covered.
 
     valid [n] (int32, nullable): only nonzero entries are candidates.  base: an earlier
     placement whose records are kept (the new records are appended after them).
     aniso: records cover their ellipsoids (anisotropic cache points) instead of spheres.
+    Learned placement (mlp given): eps_train is the tolerance the predictor was trained at
+    (default params.eps); fallback applies the coarse-record check; one_shot places every
+    predicted level's sites in one batched launch before the waves.
     """
     torch = _torch()
     n = cand.shape[0]
@@ -63,20 +81,31 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
     scratch = torch.empty((8 ** fine + 2 * n + n // 1024 + 2,), dtype=torch.int32, device=cand.device)
     site_idx = torch.empty((n,), dtype=torch.int32, device=cand.device)
     site_pts = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
+    res = PlacementResult(0)
+    n_fallback = None
     if mlp is not None:
         # predict once per cell of a 2^predict_level grid (its smallest-index candidate)
         # and give every candidate of the cell that level
         m = select_sites(cand, level, predict_level, scratch, site_idx, site_pts)
         if m:
-            feat = coarse_features(scene, site_pts[:m].contiguous(), coarse_params)
+            pts = site_pts[:m].contiguous()
+            feat = coarse_features(scene, pts, coarse_params)
             logr = mlp.predict(feat)
+            offset = 0.2 * math.log(params.eps / (eps_train or params.eps))
+            rc = None
+            if fallback:
+                # the coarse ray set's own record at the placement's tolerance
+                cp = dataclasses.replace(params, n_bands=coarse_params.n_bands, n_bins=coarse_params.n_bins,
+                                         seed=coarse_params.seed, rec_base=0, parts=0)
+                rc = compute_records(scene, pts, cp, full=False)["radius"]
+            logr, n_fallback = mlp_fallback(logr, offset, rc, logr_fallback=10.0)
+            res.predicted_sites = m
             rep = torch.empty((n,), dtype=torch.int32, device=cand.device)
             levels_by_cell(cand, predict_level, scratch, site_idx, logr, m, cell_over_radius, start_level, max_level,
                            rep, level)
     count = torch.empty((n,), dtype=torch.int32, device=cand.device)
     rgb = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
     total = prev
-    res = PlacementResult(0)
     grid = base.grid if base is not None else None
     base_grid = grid                      # the caller's grid is never rebuilt in place
     if grid is not None:
@@ -98,6 +127,21 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         query_inscatter(grid, cand, rgb, count)
         update_coverage(count, level)
 
+    if one_shot and mlp is not None:
+        # every predicted level's sites at once: level by level on a copy of the pool, each
+        # level's candidates retired after its selection, then one batched record launch
+        pool = level.clone()
+        batch = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
+        got = 0
+        for lv in range(start_level, max_level + 1):
+            m = select_sites(cand, pool, lv, scratch, site_idx, site_pts)
+            if m:
+                batch[got:got + m].copy_(site_pts[:m])
+                got += m
+            retire_level(pool, lv)
+        res.waves.append(("one-shot", got))
+        if got:
+            add_records(batch, got)
     for lv in range(start_level, max_level + 1):
         m = select_sites(cand, level, lv, scratch, site_idx, site_pts)
         res.waves.append((lv, m))
@@ -113,6 +157,8 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         left = select_sites(cand, level, fine, scratch, site_idx, site_pts)
     torch.cuda.synchronize()
     res.seconds = time.perf_counter() - t0
+    if n_fallback is not None:
+        res.fallback_sites = int(n_fallback.item())
     res.n_records = total
     res.records = {k: v[:total] for k, v in recs.items()}
     res.grid = grid

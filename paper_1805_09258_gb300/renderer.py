@@ -34,7 +34,7 @@ class FrameResult:
 
 def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int = 4, mlp=None, coarse_params=None,
                  cell_over_radius: float = 1.5, start_level: int = 2, max_level: int = 7, max_repairs: int = 8,
-                 aniso: bool = False, split: bool = False):
+                 aniso: bool = False, split: bool = False, eps_train: float = None):
     torch = _torch()
     W, H = cam.width, cam.height
     t0 = time.perf_counter()
@@ -42,7 +42,7 @@ def render_frame(scene: Scene, cam: Camera, params, steps: int = 64, stride: int
     pts, valid = march_points(scene, cam, 0, 0, w, h, stride, steps)
     caches = [replace(params, parts=1), replace(params, parts=2)] if split else [params]
     pls = [place(scene, p, pts, start_level, max_level, mlp, coarse_params, cell_over_radius, valid=valid,
-                 aniso=aniso) for p in caches]
+                 aniso=aniso, eps_train=eps_train) for p in caches]
     placement_s = sum(pl.seconds for pl in pls)
     passes = [("prepass", int(pts.shape[0]), sum(pl.n_records for pl in pls))]
     img = torch.empty((W * H, 3), dtype=torch.float32, device="cuda")

@@ -56,15 +56,16 @@ def test_predicts_held_out_radii(vrc, trained):
 
 def test_learned_placement_needs_fewer_records_at_equal_error(vrc, trained):
     """Coverage is judged by the full records' true radii in both cases, so both placements
-    honour the error tolerance; the learned one puts the coarse-wave sites where the
-    predicted radius is large (cell up to 1.5 x radius) and needs fewer records."""
+    honour the error tolerance; the predictor's levels alone (no coarse-record fallback) put
+    the coarse-wave sites where the predicted radius is large (cell up to 1.5 x radius) and
+    need fewer records."""
     from paper_1805_09258_gb300 import placement
     mlp = trained[0]
     w = W.config4(scene_seed=41)
     s = vrc.Scene.from_workload(w.scene)
     cand = torch.from_numpy(w.positions(60000, seed=441)).cuda()
     plain = placement.place(s, w.params, cand)
-    learn = placement.place(s, w.params, cand, mlp=mlp, coarse_params=COARSE, cell_over_radius=1.5)
+    learn = placement.place(s, w.params, cand, mlp=mlp, coarse_params=COARSE, cell_over_radius=1.5, fallback=False)
     for r in (plain, learn):
         _, cnt = vrc.query_inscatter(r.grid, cand)
         assert int((cnt == 0).sum()) == 0
@@ -81,3 +82,41 @@ def test_learned_placement_needs_fewer_records_at_equal_error(vrc, trained):
         errs.append(float(np.median(e)))
     print("median relative interpolation error plain / learned", errs)
     assert errs[1] <= 1.5 * errs[0] + 0.02, errs
+
+
+def test_fallback_rule_and_one_shot_placement(vrc, trained):
+    """The coarse-record check (the error at the predicted radius by the coarse ray set's
+    own Hessian, Eq. radiusAniso3D, within the tolerance) keeps exactly the predictions
+    not larger than the coarse record's radius: the placement's fallback count equals the
+    count computed here from the same predictions and coarse records.  Learned placement
+    with the fallback, one-shot or by waves, still covers every candidate, and at a
+    tolerance of eps / 10 the predictions are carried there by (1/5) log 0.1."""
+    import dataclasses
+    from paper_1805_09258_gb300 import placement
+    mlp = trained[0]
+    w = W.config4(scene_seed=41)
+    s = vrc.Scene.from_workload(w.scene)
+    cand = torch.from_numpy(w.positions(60000, seed=441)).cuda()
+    for eps in (w.params.eps, w.params.eps / 10):
+        rp = W.configs.replace(w.params, eps=eps)
+        for one_shot in (False, True):
+            r = placement.place(s, rp, cand, mlp=mlp, coarse_params=COARSE, cell_over_radius=1.5,
+                                eps_train=w.params.eps, one_shot=one_shot)
+            _, cnt = vrc.query_inscatter(r.grid, cand)
+            assert int((cnt == 0).sum()) == 0
+            assert r.predicted_sites > 1000
+        # the rule, independently: the same prediction sites (one per cell of the 2^5 grid)
+        level = torch.full((cand.shape[0],), 2, dtype=torch.int32, device="cuda")
+        scratch = torch.empty((8 ** 8 + 2 * cand.shape[0] + cand.shape[0] // 1024 + 2,), dtype=torch.int32,
+                              device="cuda")
+        site_idx = torch.empty((cand.shape[0],), dtype=torch.int32, device="cuda")
+        site_pts = torch.empty((cand.shape[0], 3), dtype=torch.float32, device="cuda")
+        m = vrc.select_sites(cand, level, 5, scratch, site_idx, site_pts)
+        pts = site_pts[:m].contiguous()
+        pred = mlp.predict(vrc.coarse_features(s, pts, COARSE)).cpu().numpy().astype(np.float64)
+        pred += 0.2 * np.log(eps / w.params.eps)
+        cp = dataclasses.replace(rp, n_bands=COARSE.n_bands, n_bins=COARSE.n_bins, seed=COARSE.seed)
+        rc = vrc.compute_records(s, pts, cp, full=False)["radius"].cpu().numpy().astype(np.float64)
+        want = int(np.sum(~(np.exp(pred) <= rc * (1 + 1e-6))))
+        assert m == r.predicted_sites
+        assert abs(r.fallback_sites - want) <= max(2, m // 1000), (r.fallback_sites, want, m)
