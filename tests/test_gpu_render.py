@@ -144,3 +144,28 @@ def test_second_grid_adds_its_lookup(vrc):
     iab, mab = vrc.render(s, ga, c, 0, 0, 48, 27, 16, grid2=gb)
     assert torch.allclose(iab, ia + ib, rtol=1e-6, atol=1e-7)
     assert torch.equal(mab, ma + mb) and int(mb.sum()) > 0
+
+
+def test_uncached_pixels_match_the_fp64_oracle(vrc):
+    """The render workload's pixels with a full record at every march point: the GPU's march
+    points, records (record ids = march point indices, so the same ray sets) and composite
+    against the FP64 oracle's (oracle/render.py, Sec. 6's uniform marching) on a 4 x 4 patch
+    at the frame's centre (250k triangles): each pixel within 1e-4 of its value plus the
+    budget of its records' near-tie decisions."""
+    import oracle.render as R
+    w = W.config5()
+    ex = w.extra
+    x0, y0, n = ex["width"] // 2 - 2, ex["height"] // 2 - 2, 4
+    cam64 = R.camera(ex["camera"], ex["forward"], ex["vfov_deg"], ex["width"], ex["height"])
+    ref = R.crop(w.scene, w.params, cam64, x0, y0, n, n, ex["steps"], track_margins=1)
+    scene = vrc.Scene.from_workload(w.scene)
+    cam = vrc.Camera.make(ex["camera"], ex["forward"], ex["vfov_deg"], ex["width"], ex["height"])
+    pts, valid = vrc.march_points(scene, cam, x0, y0, n, n, 1, ex["steps"])
+    assert np.array_equal(valid.cpu().numpy().reshape(n, n, -1)[..., 0].astype(bool), ref["valid"])
+    assert np.allclose(pts.cpu().numpy().reshape(n, n, ex["steps"], 3), ref["pts"], atol=2e-6)
+    full = vrc.compute_records(scene, pts, w.params, full=False)
+    img = vrc.composite(scene, cam, x0, y0, n, n, ex["steps"], full["L"]).cpu().numpy().reshape(n, n, 3)
+    err = np.abs(img - ref["img"])
+    allow = 1e-4 * np.abs(ref["img"]) + ref["img_budget"] + 1e-9
+    assert np.all(err <= allow), (err / allow).max()
+    assert np.all(ref["img"] > 0)
