@@ -119,8 +119,8 @@ def measured_peaks():
 
 
 # DRAM bytes per record of k_records (the pre-pass rays it loads dominate), from one ncu
-# capture of a 1,024-record launch of the mid workload: (65.71 MB + 3.17 MB) / 1,024
-K_RECORDS_DRAM_BYTES_PER_RECORD = (65.7088e6 + 3.168768e6) / 1024
+# capture of a 1,024-record launch of the mid workload: (65.88 MB + 3.11 MB) / 1,024
+K_RECORDS_DRAM_BYTES_PER_RECORD = (65.877504e6 + 3.1104e6) / 1024
 
 
 def fp32_peak_tflops(sm_mhz: float = 2070.0, n_sm: int = 152) -> float:
