@@ -410,6 +410,10 @@ int vrc_levels_from_radius(const float* d_logr, int32_t n, float cell_over_radiu
  * N = n_bands * n_bins (N = 128 for the network's 256 inputs).  Asynchronous. */
 int vrc_coarse_features(vrc_scene* scene, const float* d_pos, int32_t n, const vrc_record_params* params,
                         float* d_feat, void* stream);
+/* The same features as BF16 (round to nearest even), 512 B per record: the input of
+ * vrc_mlp_predict_bf16.  d_feat [n][2 N] BF16, 16-byte aligned.  Asynchronous. */
+int vrc_coarse_features_bf16(vrc_scene* scene, const float* d_pos, int32_t n, const vrc_record_params* params,
+                             void* d_feat, void* stream);
 
 /* The network: 256 -> 64 -> GELU -> 64 -> GELU -> 1 (log radius), BF16 weights and
  * activations as tensor-core operands, FP32 accumulation.  Parameters are one float
@@ -431,6 +435,12 @@ int vrc_mlp_get_params(const vrc_mlp* mlp, float* h_params, float* h_adam_m, flo
 int vrc_mlp_set_params(vrc_mlp* mlp, const float* h_params, const float* h_adam_m, const float* h_adam_v,
                        int64_t step);
 int vrc_mlp_predict(const vrc_mlp* mlp, const float* d_feat, int32_t n, float* d_logr, void* stream);
+/* vrc_mlp_predict from BF16 features d_feat [n][256] (row-major, 16-byte aligned): each
+ * 128-row tile is copied from HBM into the tensor cores' operand layout by the tensor
+ * memory accelerator (tiled bulk copies, 128-byte swizzle), half the bytes of the FP32
+ * path; the result equals vrc_mlp_predict on the same features rounded to BF16.
+ * VRC_ERR_UNSUPPORTED when the driver offers no tensor-map encoder.  Asynchronous. */
+int vrc_mlp_predict_bf16(const vrc_mlp* mlp, const void* d_feat, int32_t n, float* d_logr, void* stream);
 int vrc_mlp_gradient(vrc_mlp* mlp, const float* d_feat, const float* d_target, int32_t n, float* d_grad,
                      float* d_pred, void* stream);
 int vrc_mlp_train_step(vrc_mlp* mlp, const float* d_feat, const float* d_target, int32_t n, float lr,

@@ -96,6 +96,7 @@ def load_library(path: Optional[str] = None):
     L.vrc_query_inscatter.argtypes = [P, P, I32, P, P, P]
     L.vrc_query_inscatter_noalloc.argtypes = [P, I32, I32, P, I32, P, P, P]
     L.vrc_coarse_features.argtypes = [P, P, I32, P, P, P]
+    L.vrc_coarse_features_bf16.argtypes = [P, P, I32, P, P, P]
     L.vrc_march_points.argtypes = [P, P, I32, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_render.argtypes = [P, P, P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_composite.argtypes = [P, P, I32, I32, I32, I32, I32, P, P, P]
@@ -116,6 +117,7 @@ def load_library(path: Optional[str] = None):
     L.vrc_mlp_get_params.argtypes = [P, P, P, P, P]
     L.vrc_mlp_set_params.argtypes = [P, P, P, P, C.c_int64]
     L.vrc_mlp_predict.argtypes = [P, P, I32, P, P]
+    L.vrc_mlp_predict_bf16.argtypes = [P, P, I32, P, P]
     L.vrc_mlp_gradient.argtypes = [P, P, P, I32, P, P, P]
     L.vrc_mlp_train_step.argtypes = [P, P, P, I32, C.c_float, C.c_float, P, P]
     L.vrc_mlp_status.argtypes = [P]
@@ -529,16 +531,17 @@ def query_inscatter_noalloc(records: dict, q, n: Optional[int] = None, extrap_or
     return rgb, status
 
 
-def coarse_features(scene: Scene, pos, params, out=None, stream=None):
-    """vrc_coarse_features: [n, 2 N] float32 features of the coarse ray set at `pos`."""
+def coarse_features(scene: Scene, pos, params, out=None, stream=None, bf16: bool = False):
+    """vrc_coarse_features (vrc_coarse_features_bf16 with bf16=True): [n, 2 N] features of
+    the coarse ray set at `pos`, float32 (or bfloat16)."""
     torch = _torch()
     n = pos.shape[0]
     N = int(params.n_bands) * int(params.n_bins)
     if out is None:
-        out = torch.empty((n, 2 * N), dtype=torch.float32, device=pos.device)
+        out = torch.empty((n, 2 * N), dtype=torch.bfloat16 if bf16 else torch.float32, device=pos.device)
     p = record_params(params)
-    _check(load_library().vrc_coarse_features(scene.handle, _ptr(pos), n, C.byref(p), _ptr(out),
-                                              _stream_ptr(stream)), "vrc_coarse_features")
+    fn = "vrc_coarse_features_bf16" if out.dtype == torch.bfloat16 else "vrc_coarse_features"
+    _check(getattr(load_library(), fn)(scene.handle, _ptr(pos), n, C.byref(p), _ptr(out), _stream_ptr(stream)), fn)
     return out
 
 
@@ -572,12 +575,15 @@ class MLP:
                                                  None if v is None else v.ctypes.data, step), "vrc_mlp_set_params")
 
     def predict(self, feat, out=None, stream=None):
+        """Predicted log radius per feature row: float32 features through vrc_mlp_predict,
+        bfloat16 features through vrc_mlp_predict_bf16 (tiled TMA copies)."""
         torch = _torch()
         n = feat.shape[0]
+        assert feat.is_cuda and feat.is_contiguous()
         if out is None:
             out = torch.empty((n,), dtype=torch.float32, device=feat.device)
-        _check(load_library().vrc_mlp_predict(self.handle, _ptr(feat), n, _ptr(out), _stream_ptr(stream)),
-               "vrc_mlp_predict")
+        fn = "vrc_mlp_predict_bf16" if feat.dtype == torch.bfloat16 else "vrc_mlp_predict"
+        _check(getattr(load_library(), fn)(self.handle, _ptr(feat), n, _ptr(out), _stream_ptr(stream)), fn)
         return out
 
     def gradient(self, feat, target, stream=None):

@@ -20,6 +20,7 @@
 // one thread and signals an mbarrier through tcgen05.commit; results are read back with
 // tcgen05.ld (32 lanes x 32 bit per warp).  The weight-gradient accumulators E0..E2 stay
 // in tensor memory across a block's tiles and are added to global memory once.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -52,8 +53,14 @@ struct vrc_mlp {
 namespace {
 
 // ------------------------------------------------------------------ coarse features
+__device__ __forceinline__ void st_feat(float* f, size_t i, float v) { f[i] = v; }
+__device__ __forceinline__ void st_feat(__nv_bfloat16* f, size_t i, float v) { f[i] = __float2bfloat16_rn(v); }
+
+// T = float, or __nv_bfloat16 (rounded to nearest even: the value the forward pass would
+// round the float feature to when staging it as a tensor-core operand)
+template <typename T>
 __global__ void k_coarse_features(DevScene sc, const float* pos, int n, int nb, int ns, uint64_t seed,
-                                  long long rec_base, float* feat) {
+                                  long long rec_base, T* feat) {
     const int N = nb * ns;
     for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < (long long)n * N;
          item += (long long)gridDim.x * blockDim.x) {
@@ -78,8 +85,8 @@ __global__ void k_coarse_features(DevScene sc, const float* pos, int n, int nb, 
             float3 ly = sc.lpos[l] - y;
             tv += __expf(-sc.sigma_t * sqrtf(dot3(ly, ly)));
         }
-        feat[(size_t)rec * 2 * N + v] = __logf(t);
-        feat[(size_t)rec * 2 * N + N + v] = tv;
+        st_feat(feat, (size_t)rec * 2 * N + v, __logf(t));
+        st_feat(feat, (size_t)rec * 2 * N + N + v, tv);
     }
 }
 
@@ -366,6 +373,135 @@ __global__ void __launch_bounds__(128, 2) k_mlp_forward(const float* __restrict_
     tmem_free(tmem_holder, 128);
 }
 
+// ------------------------------------------------------------------ forward from BF16 features by TMA
+// The feature tile X [128 rows x 256] arrives from HBM by four tiled bulk-tensor copies
+// (cp.async.bulk.tensor.2d, box 64 features x 128 rows, 128-byte swizzle): each lands as
+// one 64-wide K block of the K-major swizzled operand layout above, so the tensor cores
+// read it as it is, with no register pass.  Rows past n are filled with zeros by the copy.
+// 512 B per record read instead of 1,024 B of FP32; predictions equal k_mlp_forward's on
+// the same features rounded to BF16 (its staging rounds them the same way).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+// One feature buffer per block and two blocks per SM (106 KB of shared memory each): one
+// block's copy overlaps the other's tensor-core work and epilogue.  (Two buffers per block
+// at one block per SM measured 0.39 ms per 1M rows against 0.22 ms: the per-tile epilogue,
+// not the copy, is then the longer part and nothing overlaps it.)
+__global__ void __launch_bounds__(128, 2) k_mlp_forward_tma(const __grid_constant__ CUtensorMap tm_x,
+                                                            const float* __restrict__ prm, int n,
+                                                            float* __restrict__ y, int* err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t mbar, mbar_x;
+    __shared__ uint32_t tmem_holder;
+    __shared__ float b1s[MLP_H], b2s[MLP_H], w3s[MLP_H];
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t sbase = smem_addr(sm);
+    if (t == 0) {
+        mbar_init(smem_addr(&mbar));
+        mbar_init(smem_addr(&mbar_x));
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_x)) : "memory");
+    }
+    tmem_alloc(&tmem_holder, 128);
+    stage_rows(sm + MlpSmem::W1, prm + OFF_W1, MLP_H, MLP_H, MLP_IN, MLP_IN);
+    stage_rows(sm + MlpSmem::W2, prm + OFF_W2, MLP_H, MLP_H, MLP_H, MLP_H);
+    if (t < MLP_H) {
+        b1s[t] = prm[OFF_B1 + t];
+        b2s[t] = prm[OFF_B2 + t];
+        w3s[t] = bf16_round(prm[OFF_W3 + t]);
+    }
+    const float b3 = prm[OFF_B3];
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    uint32_t phase = 0, phase_x = 0;
+    bool ok = true, x_pending = false, mma_pending = false;
+    for (int tile = blockIdx.x; tile * 128 < n; tile += gridDim.x) {
+        const int r0 = tile * 128;
+        const int valid = min(128, n - r0);
+        if (t == 0) {
+            mbar_expect_tx(smem_addr(&mbar_x), 128u * MLP_IN * 2u);
+#pragma unroll
+            for (int kb = 0; kb < MLP_IN / 64; ++kb)
+                tma_load_2d(sbase + MlpSmem::X + (uint32_t)(kb * 128 * 128), &tm_x, kb * 64, r0, smem_addr(&mbar_x));
+        }
+        x_pending = true;
+        ok = mbar_wait(smem_addr(&mbar_x), phase_x);
+        if (!ok) break;
+        x_pending = false;
+        phase_x ^= 1;
+        tc_fence_after();
+        if (t == 0) {
+            mma_tile(tmem + TMEM_D1, sbase + MlpSmem::X, 128, sbase + MlpSmem::W1, MLP_H, MLP_IN, MLP_H, 0);
+            mma_commit(smem_addr(&mbar));
+        }
+        mma_pending = true;
+        ok = mbar_wait(smem_addr(&mbar), phase);
+        if (!ok) break;
+        mma_pending = false;
+        phase ^= 1;
+        tc_fence_after();
+        float h[MLP_H];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float r[16];
+            tmem_ld16(tmem + lane_off + TMEM_D1 + 16 * c, r);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) h[16 * c + i] = gelu(r[i] + b1s[16 * c + i]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) st_chunk(sm + MlpSmem::FWD_H1, t, 8 * c, 128, h + 8 * c);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (t == 0) {
+            tc_fence_after();
+            mma_tile(tmem + TMEM_D2, sbase + MlpSmem::FWD_H1, 128, sbase + MlpSmem::W2, MLP_H, MLP_H, MLP_H, 0);
+            mma_commit(smem_addr(&mbar));
+        }
+        mma_pending = true;
+        ok = mbar_wait(smem_addr(&mbar), phase);
+        if (!ok) break;
+        mma_pending = false;
+        phase ^= 1;
+        tc_fence_after();
+        float acc = b3;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float r[16];
+            tmem_ld16(tmem + lane_off + TMEM_D2 + 16 * c, r);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc = fmaf(w3s[16 * c + i], gelu(r[i] + b2s[16 * c + i]), acc);
+        }
+        if (t < valid) y[r0 + t] = acc;
+        // the next tile's copy overwrites X (which h1 shares): every thread is past its reads
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok) {
+        // a wait gave up: flag it, and wait (bounded again) for this block's own copy or
+        // tensor-core work still in flight before the shared and tensor memory are released
+        if (t == 0) atomicExch(err, 1);
+        if (x_pending) mbar_wait(smem_addr(&mbar_x), phase_x);
+        if (mma_pending) mbar_wait(smem_addr(&mbar), phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem_free(tmem_holder, 128);
+}
+
 // ------------------------------------------------------------------ training (gradients)
 // part[blockIdx.x][0, MLP_NPARAM) = this block's share of d loss / d params for
 // loss = (1 / n) sum (y - t)^2, part[blockIdx.x][MLP_NPARAM] = its sum of squared residuals.
@@ -627,8 +763,20 @@ extern "C" int vrc_coarse_features(vrc_scene* s, const float* d_pos, int32_t n, 
     if (!d_pos || !d_feat || p->n_bands < 1 || p->n_bins < 1) return VRC_ERR_INVALID;
     long long items = (long long)n * p->n_bands * p->n_bins;
     int blocks = (int)std::min<long long>((items + 255) / 256, (long long)s->sm_count * 16);
-    k_coarse_features<<<blocks, 256, 0, (cudaStream_t)stream>>>(s->dev, d_pos, n, p->n_bands, p->n_bins, p->seed,
+    k_coarse_features<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(s->dev, d_pos, n, p->n_bands, p->n_bins, p->seed,
                                                                p->rec_base, d_feat);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+extern "C" int vrc_coarse_features_bf16(vrc_scene* s, const float* d_pos, int32_t n, const vrc_record_params* p,
+                                        void* d_feat, void* stream) {
+    if (!s || !p || n < 0) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    if (!d_pos || !d_feat || p->n_bands < 1 || p->n_bins < 1) return VRC_ERR_INVALID;
+    long long items = (long long)n * p->n_bands * p->n_bins;
+    int blocks = (int)std::min<long long>((items + 255) / 256, (long long)s->sm_count * 16);
+    k_coarse_features<__nv_bfloat16><<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        s->dev, d_pos, n, p->n_bands, p->n_bins, p->seed, p->rec_base, static_cast<__nv_bfloat16*>(d_feat));
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
@@ -654,6 +802,7 @@ extern "C" int vrc_mlp_create(const float* h_params, vrc_mlp** out) {
     if (!attr_set) {
         cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpSmem::FWD_END + 1024);
         cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpSmem::END + 1024);
+        cudaFuncSetAttribute(k_mlp_forward_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpSmem::FWD_END + 1024);
         attr_set = true;
     }
     *out = m;
@@ -708,6 +857,51 @@ extern "C" int vrc_mlp_predict(const vrc_mlp* m, const float* d_feat, int32_t n,
         fwd_blocks = tiles < per2 ? (tiles < 1 ? 1 : tiles) : per2;
     }
     k_mlp_forward<<<fwd_blocks, 128, MlpSmem::FWD_END + 1024, (cudaStream_t)stream>>>(m->params, d_feat, n, d_logr,
+                                                                                      m->err);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static encode_tiled_fn encode_tiled() {
+    static encode_tiled_fn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<encode_tiled_fn>(p);
+    }
+    return fn;
+}
+
+extern "C" int vrc_mlp_predict_bf16(const vrc_mlp* m, const void* d_feat, int32_t n, float* d_logr, void* stream) {
+    if (!m || n < 0) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    if (!d_feat || !d_logr) return VRC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_feat) & 15) != 0) return VRC_ERR_INVALID;   // a TMA source rule
+    encode_tiled_fn enc = encode_tiled();
+    if (!enc) return VRC_ERR_UNSUPPORTED;
+    // [n rows x 256 BF16] row-major; box 64 x 128 with the 128-byte swizzle of the operand layout
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)MLP_IN, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)MLP_IN * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(d_feat), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return VRC_ERR_INVALID;
+    // two blocks per SM, at most one per tile
+    int blocks = mlp_grid(n);
+    {
+        int tiles = (n + 127) / 128, per2 = 2 * blocks;
+        blocks = tiles < per2 ? (tiles < 1 ? 1 : tiles) : per2;
+    }
+    k_mlp_forward_tma<<<blocks, 128, MlpSmem::FWD_END + 1024, (cudaStream_t)stream>>>(map, m->params, n, d_logr,
                                                                                       m->err);
     return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }

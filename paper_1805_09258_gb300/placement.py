@@ -89,7 +89,7 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         m = select_sites(cand, level, predict_level, scratch, site_idx, site_pts)
         if m:
             pts = site_pts[:m].contiguous()
-            feat = coarse_features(scene, pts, coarse_params)
+            feat = coarse_features(scene, pts, coarse_params, bf16=True)     # read by TMA in the forward pass
             logr = mlp.predict(feat)
             offset = 0.2 * math.log(params.eps / (eps_train or params.eps))
             rc = None

@@ -109,3 +109,29 @@ def test_training_reduces_loss_and_resumes_bit_exactly(vrc):
     b.train_step(X, T, lr=3e-3)
     pa, pb = a.get_params(), b.get_params()
     assert np.array_equal(pa, pb)
+
+
+def test_bf16_features_and_tma_forward(vrc):
+    """BF16 features (vrc_coarse_features_bf16) are the FP32 features rounded to nearest
+    even, bit for bit; the forward pass that reads them by tiled TMA copies
+    (vrc_mlp_predict_bf16) gives, bit for bit, the FP32 path's predictions (whose staging
+    rounds the same features the same way), for ragged sizes over one and many tiles."""
+    w = W.config4()
+    s = vrc.Scene.from_workload(w.scene)
+    pos = torch.from_numpy(w.positions(3000, seed=71)).cuda()
+    f32 = vrc.coarse_features(s, pos, COARSE)
+    b16 = vrc.coarse_features(s, pos, COARSE, bf16=True)
+    assert b16.dtype == torch.bfloat16
+    assert torch.equal(b16, f32.to(torch.bfloat16))
+    mlp = vrc.MLP(perturbed_params(3))
+    for n in (1, 127, 128, 129, 3000):
+        a = mlp.predict(f32[:n].contiguous())
+        b = mlp.predict(b16[:n].contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), n
+    big = torch.from_numpy(realistic_features(70001, 9)).cuda()
+    a = mlp.predict(big)
+    b = mlp.predict(big.to(torch.bfloat16).contiguous())
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert mlp.status() == 0
