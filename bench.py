@@ -591,8 +591,10 @@ def run_flat(args, w):
 
 def run_mlp(args):
     """Extra measurement (not the default line): the learned radius predictor's kernels.
-    Inference: 1M feature rows (256 float32 each) -> log radius; a pass reads 1,028 B per
-    row, so its roofline is HBM (41,088 FLOP per row on the tensor pipe: 40 FLOP/B).
+    Inference: 1M feature rows -> log radius, from BF16 features brought in by tiled TMA
+    copies (k_mlp_forward_tma: 516 B per row read and written) and from FP32 features
+    (k_mlp_forward: 1,028 B per row); both are HBM-bound (41,088 FLOP per row on the tensor
+    pipe: 80 and 40 FLOP/B).
     Training: AdamW steps on 4,096-row batches (forward + backward, about 3 x the forward
     FLOP per row), a latency-bound chain of small launches."""
     import torch
@@ -609,19 +611,25 @@ def run_mlp(args):
     flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device="cuda")
     mlp = vrc.MLP(M.init_params(5))
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        mlp.predict(feat, out)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mlp.predict(feat, out)
-        e1.record(stream)
-        ts.append((e0, e1))
-    torch.cuda.synchronize()
-    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b in ts]))
+    feat16 = feat.to(torch.bfloat16).contiguous()
+
+    def time_forward(x):
+        for _ in range(args.warmup):
+            mlp.predict(x, out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mlp.predict(x, out)
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ts]))
+
+    fwd32_ms = time_forward(feat)
+    fwd_ms = time_forward(feat16)
     bsz, n_steps = 4096, 200
     for s_ in range(args.warmup):
         mlp.train_step(feat[:bsz], tgt[:bsz], 1e-3)
@@ -637,16 +645,19 @@ def run_mlp(args):
     peaks = measured_peaks() or {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    bytes_row, flop_row = 256 * 4 + 4, 2 * (256 * 64 + 64 * 64 + 64)
+    bytes_row, flop_row = 256 * 2 + 4, 2 * (256 * 64 + 64 * 64 + 64)
     fwd_gbs = n * bytes_row / (fwd_ms * 1e-3) / 1e9
+    fwd32_gbs = n * (256 * 4 + 4) / (fwd32_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": n / (fwd_ms * 1e-3), "unit": "radius predictions/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd_ms, "higher_is_better": True,
             "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
             "config": {"workload": "learned radius predictor: 256-64-64-1 GELU MLP, 1M rows; training batches of 4,096",
                        "l2": "flushed between timed passes (256 MB write)"},
-            "roofline": {"kernel": "k_mlp_forward", "bound": "hbm", "achieved": fwd_gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": fwd_gbs / hbm, "traffic": None,
+            "roofline": {"kernel": "k_mlp_forward_tma (BF16 features)", "bound": "hbm", "achieved": fwd_gbs,
+                         "peak": hbm, "unit": "GB/s", "frac": fwd_gbs / hbm, "traffic": None,
                          "tensor_tflops": n * flop_row / (fwd_ms * 1e-3) / 1e12, "bf16_peak_tflops": bf16},
+            "forward_fp32_features": {"kernel": "k_mlp_forward", "ms": fwd32_ms, "predictions_per_s": n / (fwd32_ms * 1e-3),
+                                      "achieved_gbs": fwd32_gbs, "frac": fwd32_gbs / hbm},
             "train_step_ms": step_ms, "train_rows_per_s": bsz / (step_ms * 1e-3),
             "train_tflops": 3 * flop_row * bsz / (step_ms * 1e-3) / 1e12}
     print(json.dumps(line), flush=True)
@@ -893,30 +904,26 @@ def run_render(args, w):
                      "eps": eps, "passes": len(fr.passes), "misses_repaired": fr.misses,
                      "records_ss_ms": None if fr.placement2 is None else [fr.placement.n_records,
                                                                           fr.placement2.n_records]}
-    # equal-error comparison: plain frame time interpolated at each other run's error (against
-    # the FP64 crop when it is there, else the 16-crop reference)
+    # equal-error comparison against the FP64 crop when it is there (else the 16-crop
+    # reference): the plain frame time at equal error is that of the fastest plain run whose
+    # error is at most this run's (the plain runs' error is not monotone in the tolerance on a
+    # noise-limited 64 x 64 crop, so no interpolation between them)
     key = "rel_rmse_fp64_crop" if fp64 is not None else "rel_rmse"
-    plain = sorted((v[key], v["frame_ms"], v["records"]) for k, v in res.items() if k.startswith("plain_eps"))
+    plain = [(v[key], v["frame_ms"], v["records"], k) for k, v in res.items() if k.startswith("plain_eps")]
     equal = {}
     for k, v in res.items():
         if k.startswith("plain_eps"):
             continue
         e = v[key]
-        lo = [p for p in plain if p[0] <= e]
-        hi = [p for p in plain if p[0] >= e]
-        if lo and hi:
-            a, b = lo[-1], hi[0]
-            if a[0] == b[0]:
-                t, n = a[1], a[2]
-            else:
-                f_ = (math.log(e) - math.log(a[0])) / (math.log(b[0]) - math.log(a[0]))
-                t = math.exp(math.log(a[1]) + f_ * (math.log(b[1]) - math.log(a[1])))
-                n = math.exp(math.log(a[2]) + f_ * (math.log(b[2]) - math.log(a[2])))
-            equal[k] = {key: e, "plain_frame_ms_at_equal_error": t, "frame_ms": v["frame_ms"],
-                        "speedup": t / v["frame_ms"], "plain_records_at_equal_error": n,
-                        "records": v["records"]}
+        ok = [p for p in plain if p[0] <= e]
+        if ok:
+            best = min(ok, key=lambda p: p[1])
+            equal[k] = {key: e, "plain_run": best[3], "plain_error": best[0], "plain_frame_ms": best[1],
+                        "frame_ms": v["frame_ms"], "speedup": best[1] / v["frame_ms"],
+                        "plain_records": best[2], "records": v["records"]}
         else:
-            equal[k] = {"mean_rel_err": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
+            equal[k] = {key: e, "better_than_every_plain_run": True, "frame_ms": v["frame_ms"],
+                        "plain_best_error": min(p[0] for p in plain)}
     n_q = Wd * Hd * steps
     base = res[f"learned_eps{rp.eps:g}"]
     line = {"metric": METRIC, "value": n_q / (base["frame_ms"] * 1e-3), "unit": "march points/s (whole frame)",

@@ -82,9 +82,10 @@ def march(oscene: OracleScene, scene, cam: dict, px, py, steps: int):
 
 
 def crop(scene, params, cam: dict, x0: int, y0: int, w: int, h: int, steps: int, n_threads: int = 0,
-         track_margins: int = 0) -> dict:
+         track_margins: int = 0, rec_base: int = 0) -> dict:
     """The FP64 reference of the pixels [x0, x0 + w) x [y0, y0 + h): a full oracle record
-    (params; record ids = march point indices) at every march point, composited.  With
+    (params; record ids = rec_base + march point index, march points in pixel-row order, `steps`
+    per pixel) at every march point, composited.  With
     track_margins, img_budget bounds the change of each pixel that the records' near-tie
     decisions can make (their radiance budgets, weighted as the pixel sums them)."""
     osc = OracleScene(scene)
@@ -96,7 +97,7 @@ def crop(scene, params, cam: dict, x0: int, y0: int, w: int, h: int, steps: int,
     sel = np.repeat(ok, steps)
     ids = np.flatnonzero(sel)
     if ids.size:
-        r = records(osc, params, flat[ids], rec_ids=ids, n_threads=n_threads, track_margins=track_margins)
+        r = records(osc, params, flat[ids], rec_ids=rec_base + ids, n_threads=n_threads, track_margins=track_margins)
         L[ids] = r["L"]
         bud[ids] = r["bud_L"]
     img = (wts[..., None] * L.reshape(-1, steps, 3)).sum(axis=1)
@@ -113,7 +114,8 @@ def render_crop_path(size: int = 64) -> str:
 
 
 def central_crop(size: int = 64, n_threads: int = 0, out: str = None, verbose: bool = False) -> dict:
-    """The render workload's central size x size pixels (cached)."""
+    """The render workload's central size x size pixels (cached); record ids are the march
+    points' indices over the whole crop (pixel rows in order, `steps` points per pixel)."""
     import workloads as W
     w = W.config5()
     ex = w.extra
@@ -129,7 +131,8 @@ def central_crop(size: int = 64, n_threads: int = 0, out: str = None, verbose: b
     for r0 in range(0, size, rows):
         part = path + f".rows{r0}.npz"
         if not os.path.exists(part):
-            p = crop(w.scene, w.params, cam, x0, y0 + r0, size, min(rows, size - r0), ex["steps"], n_threads)
+            p = crop(w.scene, w.params, cam, x0, y0 + r0, size, min(rows, size - r0), ex["steps"], n_threads,
+                     rec_base=r0 * size * ex["steps"])
             os.makedirs(os.path.dirname(path), exist_ok=True)
             np.savez(part + ".tmp.npz", **p)
             os.replace(part + ".tmp.npz", part)
