@@ -60,7 +60,7 @@ class _Params(C.Structure):
                 ("omega_o", C.c_float * 3), ("seed", C.c_uint64), ("ff_signed", C.c_int),
                 ("extrap_order", C.c_int), ("r_min", C.c_float), ("r_max", C.c_float),
                 ("rec_base", C.c_int64), ("general_derivs", C.c_int), ("track_margins", C.c_int),
-                ("surface_only", C.c_int)]
+                ("surface_only", C.c_int), ("lo_grad", C.c_int)]
 
 
 _lib = None
@@ -161,6 +161,7 @@ def make_params(rp, general_derivs: int = 1, track_margins: int = 0, surface_onl
     p.r_min, p.r_max = rp.r_min, rp.r_max
     p.rec_base = rp.rec_base
     p.general_derivs, p.track_margins, p.surface_only = general_derivs, track_margins, surface_only
+    p.lo_grad = int(getattr(rp, "lo_grad", 0))
     return p
 
 

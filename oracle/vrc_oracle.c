@@ -141,6 +141,7 @@ typedef struct {
     int general_derivs;      /* 1: Eqs. SSSegALGradient/Hessian; 0: simplified Eqs. (g = 0) */
     int track_margins;       /* 1: record decision margins (slower) */
     int surface_only;        /* 1: skip medium shells (closed-form sphere test) */
+    int lo_grad;             /* 1: keep grad L_o of medium vertices (f4, one light; see cell_radiance) */
 } orc_params;
 
 /* ------------------------------------------------------------ vector utils */
@@ -688,8 +689,15 @@ static int formfactor(v3 x, v3 y1, v3 y2, v3 y3, int ff_signed, sfun* F) {
  * the simplified Eqs. SSSegALGradientSimp/HessianSimp (isotropic: grad f = H f = 0). */
 typedef struct { double L[3]; double g[3][3]; double H[3][3][3]; } cellout;
 
+/* Outgoing radiance of a furthest vertex as a function of x (the extension beyond Sec. 4's
+ * grad L_o = 0 that Sec. 7 discusses): a medium vertex scatters its light with the HG phase,
+ * so its radiance toward x is L_o(x) = L_o(x_c) f(l . w(x)) / f(l . w(x_c)), l the light's
+ * propagation direction at the vertex, w(x) the unit direction from the vertex to x, x_c the
+ * record centre where L_o was computed.  lp_far[q] = l and f0_far[q] = f(l . w(x_c)) per
+ * furthest vertex (f0 <= 0: constant L_o, as for Lambertian surfaces); NULL: all constant. */
 static int cell_radiance(v3 x, v3 y1, v3 y2, v3 y3, int n_far, const v3* y_far, const double* const* Lo_far,
-                         double sigma_t, double g, v3 wo, double weight, int general, int ff_signed, cellout* out) {
+                         double sigma_t, double g, v3 wo, double weight, int general, int ff_signed, cellout* out,
+                         const v3* lp_far, const double* f0_far) {
     sfun F, f;
     memset(out, 0, sizeof(*out));
     int ok = formfactor(x, y1, y2, y3, ff_signed, &F);
@@ -708,6 +716,18 @@ static int cell_radiance(v3 x, v3 y1, v3 y2, v3 y3, int n_far, const v3* y_far, 
         for (int q = 0; q < n_far; ++q) {
             sfun T;
             transmittance(x, y_far[q], sigma_t, &T);
+            if (lp_far && f0_far && f0_far[q] > 0.0) {
+                /* Eq. reducedRadianceDerivatives with grad L_o kept: T u, u = L_o(x) / L_o(x_c) */
+                sfun fv, Tu;
+                phase(x, y_far[q], lp_far[q], g, &fv);
+                double iu = 1.0 / f0_far[q];
+                Tu.v = T.v * fv.v * iu;
+                for (int i = 0; i < 3; ++i) Tu.g[i] = (T.v * fv.g[i] + fv.v * T.g[i]) * iu;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        Tu.H[i][j] = (T.v * fv.H[i][j] + T.g[i] * fv.g[j] + fv.g[i] * T.g[j] + fv.v * T.H[i][j]) * iu;
+                T = Tu;
+            }
             double lo = Lo_far[q][c] * weight / (double)n_far;
             Lr += lo * T.v;
             for (int i = 0; i < 3; ++i) gLr[i] += lo * T.g[i];
@@ -1232,6 +1252,20 @@ static decision_t* find_decision(ffsum* acc, int kind, int k, int v) {
     return d;
 }
 
+/* f4 (lo_grad): the light's propagation direction at medium vertex v of shell k (position y)
+ * and the HG phase toward the record centre, where the vertex radiance was computed (the
+ * direction to the centre is -d_v).  Returns 0 (constant L_o) for surface vertices, closed
+ * vertices and when lo_grad is off. */
+static int vertex_light(const orc_scene* s, const shells_t* S, const orc_params* p, int k, int v, int open, v3 y,
+                        v3* lp, double* f0) {
+    *f0 = 0.0;
+    if (!p->lo_grad || k == 0 || !open || s->in.n_lights != 1) return 0;
+    v3 l = sub(y, ldv(s->in.light_pos));
+    *lp = scl(l, 1.0 / norm(l));
+    *f0 = orc_hg(-dot(*lp, S->dir[v]), (double)s->in.g);
+    return 1;
+}
+
 /* One cell of shell k with the decisions alts[q] of its vertices taken the other way.
  * far_set (bit mask) overrides the furthest vertices when nonzero.  Fills *co (zero for a
  * dark or degenerate cell) and *near_set: the vertices whose parameter is within FP32
@@ -1255,19 +1289,22 @@ static int eval_cell(const orc_scene* s, const shells_t* S, const orc_params* p,
     if (near_set) *near_set = nearm;
     if (open_set) *open_set = openm;
     int fs = far_set ? far_set : canon;
-    v3 yf[3];
+    v3 yf[3], lpf[3];
+    double f0f[3];
     const double* Lf[3];
     int nf = 0, dark = 1;
     for (int q = 0; q < 3; ++q)
         if (fs & (1 << q)) {
-            yf[nf] = y[q]; Lf[nf] = Lo[q]; ++nf;
+            yf[nf] = y[q]; Lf[nf] = Lo[q];
+            vertex_light(s, S, p, k, vi[q], op[q], y[q], &lpf[nf], &f0f[nf]);
+            ++nf;
             if (Lo[q][0] != 0.0 || Lo[q][1] != 0.0 || Lo[q][2] != 0.0) dark = 0;
         }
     memset(co, 0, sizeof(*co));
     if (dark) return 1;
     v3 wo = ldv(p->omega_o);
     int ok = cell_radiance(x_eval, y[0], y[1], y[2], nf, yf, Lf, s->sigma_t, (double)s->in.g, wo, weight,
-                           p->general_derivs, p->ff_signed, co);
+                           p->general_derivs, p->ff_signed, co, lpf, f0f);
     if (!ok) memset(co, 0, sizeof(*co));
     return ok;
 }
@@ -1384,7 +1421,7 @@ static void cell_budget(const orc_scene* s, const shells_t* S, const orc_params*
         cellout cu;
         v3 wo = ldv(p->omega_o);
         if (cell_radiance(x_eval, y[0], y[1], y[2], 1, &yf, Up, s->sigma_t, (double)s->in.g, wo, weight,
-                          p->general_derivs, p->ff_signed, &cu)) {
+                          p->general_derivs, p->ff_signed, &cu, NULL, NULL)) {
             static const cellout zero_cell;
             double nL[3], ng[3], nH[3];
             cell_diff_norms(&cu, &zero_cell, nL, ng, nH);
@@ -1421,10 +1458,15 @@ static void ff_accumulate(const orc_scene* s, const shells_t* S, const orc_param
             /* furthest vertices (R9): all vertices at the largest t */
             double tmx = fmax(key[0], fmax(key[1], key[2]));
             int nf = 0;
-            v3 yf[3];
+            v3 yf[3], lpf[3];
+            double f0f[3];
             const double* Lf[3];
             for (int q = 0; q < 3; ++q)
-                if (key[q] == tmx) { yf[nf] = y[q]; Lf[nf] = Lo[q]; ++nf; }
+                if (key[q] == tmx) {
+                    yf[nf] = y[q]; Lf[nf] = Lo[q];
+                    vertex_light(s, S, p, k, vi[q], k > 0 && vertex_open(S, p, k, vi[q]), y[q], &lpf[nf], &f0f[nf]);
+                    ++nf;
+                }
             if (p->track_margins && !S->full) cell_budget(s, S, p, x_eval, k, c, vi, weight, acc);
             int dark = 1;
             for (int q = 0; q < nf; ++q)
@@ -1432,7 +1474,7 @@ static void ff_accumulate(const orc_scene* s, const shells_t* S, const orc_param
             if (dark) continue;
             cellout co;
             int ok = cell_radiance(x_eval, y[0], y[1], y[2], nf, yf, Lf, s->sigma_t, (double)s->in.g, wo, weight,
-                                   p->general_derivs, p->ff_signed, &co);
+                                   p->general_derivs, p->ff_signed, &co, lpf, f0f);
             if (!ok) { acc->n_degen++; continue; }
             double hn = 0.0;
             for (int i = 0; i < 3; ++i)
@@ -1746,7 +1788,7 @@ int orc_cell(const double* x, const double* y1, const double* y2, const double* 
         if (far_mask & (1 << q)) { yf[nf] = y[q]; Lf[nf] = Lo + 3 * q; ++nf; }
     cellout co;
     int ok = cell_radiance(mk(x[0], x[1], x[2]), y[0], y[1], y[2], nf, yf, Lf, sigma_t, g, mk(wo[0], wo[1], wo[2]),
-                           weight, general, ff_signed, &co);
+                           weight, general, ff_signed, &co, NULL, NULL);
     for (int c = 0; c < 3; ++c) {
         out[c] = co.L[c];
         for (int i = 0; i < 3; ++i) out[3 + 3 * c + i] = co.g[c][i];

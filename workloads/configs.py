@@ -45,6 +45,7 @@ class RecordParams:
     r_max: float = 0.5
     rec_base: int = 0
     parts: int = 0          # 0 whole radiance, 1 surface shell (SS cache), 2 medium shells (MS cache)
+    lo_grad: int = 0        # 1: medium vertices' radiance varies with x through their phase function
 
     @property
     def n_rays(self) -> int:
