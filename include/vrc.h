@@ -86,7 +86,13 @@ void vrc_destroy_scene(vrc_scene* scene);
  *   parts             0: the whole in-scattered radiance (surface and medium shells);
  *                     1: surface shell only (the single-scattering cache of Sec. 6);
  *                     2: medium shells only (the multiple-scattering cache of Sec. 6).
- *                     With 1 or 2 every output (L, grad, hess, radius, ...) is that part. */
+ *                     With 1 or 2 every output (L, grad, hess, radius, ...) is that part.
+ *   lo_grad           1: a medium vertex's outgoing radiance varies with x through the HG
+ *                     phase of the light it scatters toward x (L_o(x) = L_o(x_c) f(l . w(x)) /
+ *                     f(l . w(x_c)), l the light's direction of travel at the vertex, w(x) the
+ *                     direction from it to x), so Eq. reducedRadianceDerivatives keeps grad L_o
+ *                     and H L_o (Sec. 7 names this extension); needs exactly one light, else
+ *                     VRC_ERR_UNSUPPORTED.  0 (default): L_o constant (Sec. 4). */
 typedef struct {
     int32_t n_bands, n_bins;
     float dt, eps;
@@ -97,6 +103,7 @@ typedef struct {
     float r_min, r_max;
     int64_t rec_base;
     int32_t parts;
+    int32_t lo_grad;
 } vrc_record_params;
 
 /* Caller-allocated device outputs of vrc_compute_records, one row per record.

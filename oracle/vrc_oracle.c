@@ -53,6 +53,12 @@
  *      with |lambda_i|, the same clamps) along its eigenvector; a query's distance
  *      ratio |x' - x_k| / R_k becomes the ellipsoidal norm sqrt(D^T M_k D), with
  *      M_k = sum_i v_i v_i^T / R_i^2, in the membership test and in d = 1 - ratio.
+ *  R18 lo_grad (optional, off by default; Sec. 7's extension of R11): an open medium
+ *      vertex y scatters its light toward x, so its radiance toward x is
+ *      L_o(x_c) f(l . w(x)) / f(l . w(x_c)), l = (y - p_light)/|y - p_light|,
+ *      w(x) = (x - y)/|x - y|: the ratio is 1 at the centre and carries grad L_o and
+ *      H L_o into the product rule.  One light only (with several, each light's share
+ *      of L_o would need its own factor); surface and clamped vertices stay constant.
  */
 #include <math.h>
 #include <pthread.h>
@@ -141,7 +147,7 @@ typedef struct {
     int general_derivs;      /* 1: Eqs. SSSegALGradient/Hessian; 0: simplified Eqs. (g = 0) */
     int track_margins;       /* 1: record decision margins (slower) */
     int surface_only;        /* 1: skip medium shells (closed-form sphere test) */
-    int lo_grad;             /* 1: keep grad L_o of medium vertices (f4, one light; see cell_radiance) */
+    int lo_grad;             /* 1: keep grad L_o of medium vertices (one light; see cell_radiance) */
 } orc_params;
 
 /* ------------------------------------------------------------ vector utils */
@@ -1252,7 +1258,7 @@ static decision_t* find_decision(ffsum* acc, int kind, int k, int v) {
     return d;
 }
 
-/* f4 (lo_grad): the light's propagation direction at medium vertex v of shell k (position y)
+/* lo_grad: the light's propagation direction at medium vertex v of shell k (position y)
  * and the HG phase toward the record centre, where the vertex radiance was computed (the
  * direction to the centre is -d_v).  Returns 0 (constant L_o) for surface vertices, closed
  * vertices and when lo_grad is off. */

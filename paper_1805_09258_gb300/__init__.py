@@ -41,7 +41,7 @@ class RecordParamsC(C.Structure):
     _fields_ = [("n_bands", C.c_int32), ("n_bins", C.c_int32), ("dt", C.c_float), ("eps", C.c_float),
                 ("omega_o", C.c_float * 3), ("seed", C.c_uint64), ("ff_signed", C.c_int32),
                 ("extrap_order", C.c_int32), ("r_min", C.c_float), ("r_max", C.c_float), ("rec_base", C.c_int64),
-                ("parts", C.c_int32)]
+                ("parts", C.c_int32), ("lo_grad", C.c_int32)]
 
 
 class RecordsView(C.Structure):
@@ -161,6 +161,7 @@ def record_params(rp) -> RecordParamsC:
     p.r_min, p.r_max = float(rp.r_min), float(rp.r_max)
     p.rec_base = int(getattr(rp, "rec_base", 0))
     p.parts = int(getattr(rp, "parts", 0))
+    p.lo_grad = int(getattr(rp, "lo_grad", 0))
     return p
 
 

@@ -47,6 +47,7 @@ struct RecArgs {
     const float* pre_Lo;         // [item - item_base][pre_stride][3]
     int pre_stride;              // rays per pre-pass slot (the largest ray set of the launch)
     int item_base, item_end;     // work items of the current batch (positions in `order`)
+    int lo_grad;                 // medium vertices' radiance varies with x (one light)
 };
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -113,6 +114,37 @@ __device__ float3 surface_radiance(const DevScene& sc, int prim, float3 y, float
     return L;
 }
 
+// HG phase f(w_i . wo) with w_i = w / |w|, w = x - y (a point y seen from x), and its
+// gradient and Hessian (6 entries) with respect to x
+__device__ __forceinline__ void hg_dx(float3 w, float3 wo, float g, float& fv, float (&gf)[3], float (&Hf)[6]) {
+    float iw = rsqrtf(dot3(w, w));
+    float3 wi = w * iw;
+    float mu = dot3(wi, wo);
+    float q = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
+    float rq = rsqrtf(q);
+    float cg = (1.0f - g * g) * (0.25f / VRC_PI_F);
+    float rq3 = rq * rq * rq;
+    fv = cg * rq3;
+    float f1 = 3.0f * g * cg * rq3 * rq * rq;             // df/dmu
+    float f2 = 5.0f * g * f1 * rq * rq;                   // d2f/dmu2
+    float3 gm = (wo - wi * mu) * iw;                      // grad mu
+    float iw2 = iw * iw;
+    // H mu = (-wo wi^T - wi wo^T - mu I + 3 mu wi wi^T) / |w|^2
+    float Hm[6] = {(-2.f * wo.x * wi.x - mu + 3.f * mu * wi.x * wi.x) * iw2,
+                   (-wo.x * wi.y - wi.x * wo.y + 3.f * mu * wi.x * wi.y) * iw2,
+                   (-wo.x * wi.z - wi.x * wo.z + 3.f * mu * wi.x * wi.z) * iw2,
+                   (-2.f * wo.y * wi.y - mu + 3.f * mu * wi.y * wi.y) * iw2,
+                   (-wo.y * wi.z - wi.y * wo.z + 3.f * mu * wi.y * wi.z) * iw2,
+                   (-2.f * wo.z * wi.z - mu + 3.f * mu * wi.z * wi.z) * iw2};
+    gf[0] = f1 * gm.x; gf[1] = f1 * gm.y; gf[2] = f1 * gm.z;
+    Hf[0] = f2 * gm.x * gm.x + f1 * Hm[0];
+    Hf[1] = f2 * gm.x * gm.y + f1 * Hm[1];
+    Hf[2] = f2 * gm.x * gm.z + f1 * Hm[2];
+    Hf[3] = f2 * gm.y * gm.y + f1 * Hm[3];
+    Hf[4] = f2 * gm.y * gm.z + f1 * Hm[4];
+    Hf[5] = f2 * gm.z * gm.z + f1 * Hm[5];
+}
+
 // ----------------------------------------------------------------- one cell
 // Cell j with vertices r_q = y_q - x (q = 0..2) at ray parameters t_q and radiance
 // Lo_q.  Writes the 32 values: L_j (3), grad L_j (3 x 3), H L_j (3 x 6), the Frobenius
@@ -124,8 +156,15 @@ __device__ float3 surface_radiance(const DevScene& sc, int prim, float3 y, float
 // H A = 0.  Here grad B = -sum_i c_i r_i with c_i = (rho_j rho_k + r_j.r_k)/rho_i + rho_j
 // + rho_k, and H B = (sum c_i) I - sum_i r_i grad c_i^T; the Hessian of Omega is the
 // symmetric form 2[-A HB/D - (2/D^2)(AB(aa^T - bb^T) + (B^2-A^2)/2 (ab^T + ba^T))].
+// LOG (lo_grad, medium shells): a furthest vertex's radiance toward x is L_o(x_c) u(x), u the
+// HG phase of its light toward x over its value toward the centre (u = 1 at x); u folds into
+// the transmittance factor by the product rule (Eq. reducedRadianceDerivatives with grad L_o
+// kept), for the open vertices (medium points: bit q of open_mask; a clamped vertex is a
+// Lambertian surface point, constant toward x).  xl = x - (the light's position).
+template <bool LOG>
 __device__ __forceinline__ int cell_eval(const float3 (&r)[3], const float (&t)[3], const float3 (&Lo)[3],
-                                         float sigma_t, float g, float3 wo, int ff_signed, float (&v)[32]) {
+                                         float sigma_t, float g, float3 wo, int ff_signed, float (&v)[32],
+                                         float3 xl = f3(0.f, 0.f, 0.f), unsigned open_mask = 0u) {
     float tmx = fmaxf(t[0], fmaxf(t[1], t[2]));
     bool far0 = t[0] == tmx, far1 = t[1] == tmx, far2 = t[2] == tmx;
     bool lit = (far0 && (Lo[0].x != 0.f || Lo[0].y != 0.f || Lo[0].z != 0.f)) ||
@@ -197,33 +236,7 @@ __device__ __forceinline__ int cell_eval(const float3 (&r)[3], const float (&t)[
     if (g == 0.0f) {
         fv = 0.25f / VRC_PI_F;
     } else {
-        float3 w = (r[0] + r[1] + r[2]) * (-1.0f / 3.0f);
-        float iw = rsqrtf(dot3(w, w));
-        float3 wi = w * iw;
-        float mu = dot3(wi, wo);
-        float q = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
-        float rq = rsqrtf(q);
-        float cg = (1.0f - g * g) * (0.25f / VRC_PI_F);
-        float rq3 = rq * rq * rq;
-        fv = cg * rq3;
-        float f1 = 3.0f * g * cg * rq3 * rq * rq;             // df/dmu
-        float f2 = 5.0f * g * f1 * rq * rq;                   // d2f/dmu2
-        float3 gm = (wo - wi * mu) * iw;                      // grad mu
-        float iw2 = iw * iw;
-        // H mu = (-wo wi^T - wi wo^T - mu I + 3 mu wi wi^T) / |w|^2
-        float Hm[6] = {(-2.f * wo.x * wi.x - mu + 3.f * mu * wi.x * wi.x) * iw2,
-                       (-wo.x * wi.y - wi.x * wo.y + 3.f * mu * wi.x * wi.y) * iw2,
-                       (-wo.x * wi.z - wi.x * wo.z + 3.f * mu * wi.x * wi.z) * iw2,
-                       (-2.f * wo.y * wi.y - mu + 3.f * mu * wi.y * wi.y) * iw2,
-                       (-wo.y * wi.z - wi.y * wo.z + 3.f * mu * wi.y * wi.z) * iw2,
-                       (-2.f * wo.z * wi.z - mu + 3.f * mu * wi.z * wi.z) * iw2};
-        gf[0] = f1 * gm.x; gf[1] = f1 * gm.y; gf[2] = f1 * gm.z;
-        Hf[0] = f2 * gm.x * gm.x + f1 * Hm[0];
-        Hf[1] = f2 * gm.x * gm.y + f1 * Hm[1];
-        Hf[2] = f2 * gm.x * gm.z + f1 * Hm[2];
-        Hf[3] = f2 * gm.y * gm.y + f1 * Hm[3];
-        Hf[4] = f2 * gm.y * gm.z + f1 * Hm[4];
-        Hf[5] = f2 * gm.z * gm.z + f1 * Hm[5];
+        hg_dx((r[0] + r[1] + r[2]) * (-1.0f / 3.0f), wo, g, fv, gf, Hf);
     }
     // ---- reduced radiance at the tied furthest vertices, product rule, RGB scatter
     float inv_m = 1.0f / (float)((int)far0 + (int)far1 + (int)far2);
@@ -240,6 +253,23 @@ __device__ __forceinline__ int cell_eval(const float3 (&r)[3], const float (&t)[
         float h1 = st_T * (ir + sigma_t), h0 = -st_T * ir; // H T = st T [(1/rho + st) u u^T - I/rho]
         float HT[6] = {h1 * u.x * u.x + h0, h1 * u.x * u.y, h1 * u.x * u.z,
                        h1 * u.y * u.y + h0, h1 * u.y * u.z, h1 * u.z * u.z + h0};
+        if (LOG && ((open_mask >> q) & 1u) && g != 0.0f) {
+            // the light's direction of travel at the vertex y = x + r_q, and the vertex's
+            // phase toward x (w = x - y = -r_q) with its x-derivatives, divided by its value
+            float3 lp = r[q] + xl;
+            lp = lp * rsqrtf(dot3(lp, lp));
+            float fu, gu[3], Hu[6];
+            hg_dx(r[q] * -1.0f, lp, g, fu, gu, Hu);
+            const float ifu = 1.0f / fu;
+            float gTa0[3] = {gT.x, gT.y, gT.z};
+#pragma unroll
+            for (int e = 0; e < 3; ++e) gu[e] *= ifu;
+            const int ia[6] = {0, 0, 0, 1, 1, 2}, ja[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int e = 0; e < 6; ++e)
+                HT[e] += gTa0[ia[e]] * gu[ja[e]] + gu[ia[e]] * gTa0[ja[e]] + T * Hu[e] * ifu;
+            gT = f3(gT.x + T * gu[0], gT.y + T * gu[1], gT.z + T * gu[2]);
+        }
         // P = Omega T
         float P = Om * T;
         float gP[3] = {T * gO.x + Om * gT.x, T * gO.y + Om * gT.y, T * gO.z + Om * gT.z};
@@ -406,7 +436,7 @@ __device__ __forceinline__ void dbg_set_lit(const vrc_records_view& o, int rec, 
 #define VRC_RECORDS_REGS 85
 #endif
 
-template <int NT>
+template <int NT, bool LOG = false>
 __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records(DevScene sc, RecArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ float4 smem4[];
@@ -604,15 +634,18 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * VRC_RECORDS_REGS)) k_records
                         cell_verts(c, vi);
                         float3 rr[3], Lo[3];
                         float tt[3];
+                        unsigned open_mask = 0u;
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             float4 rv = ray[vi[q]];
-                            float tq = (k == 0 || !(tk < rv.w)) ? rv.w : tk;
+                            const bool open = k > 0 && tk < rv.w;
+                            float tq = open ? tk : rv.w;
+                            open_mask |= (unsigned)open << q;
                             tt[q] = tq;
                             rr[q] = f3(rv.x * tq, rv.y * tq, rv.z * tq);
                             Lo[q] = f3(Lrk[vi[q]], Lgk[vi[q]], Lbk[vi[q]]);
                         }
-                        m = cell_eval(rr, tt, Lo, sigma_t, g, a.wo, a.ff_signed, v);
+                        m = cell_eval<LOG>(rr, tt, Lo, sigma_t, g, a.wo, a.ff_signed, v, x - sc.lpos[0], open_mask);
                     }
                     lit_cells += m > 0 ? 1 : 0;
                     far_evals += m;
@@ -1176,9 +1209,9 @@ static int batch_records(long long cap, int stride, int n) {
     return (int)(b < 1 ? 1 : (b > n ? n : b));
 }
 
-template <int NT>
+template <int NT, bool LOG = false>
 int launch_records(vrc_scene* s, const RecArgs& a0, size_t smem, cudaStream_t st) {
-    auto kfn = k_records<NT>;
+    auto kfn = k_records<NT, LOG>;
     if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return VRC_ERR_UNSUPPORTED;
     int per_sm = 0;
@@ -1322,6 +1355,7 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
         return VRC_ERR_INVALID;
     if (p->parts < 0 || p->parts > 2) return VRC_ERR_INVALID;
     if (nb > 256 || ns > 512) return VRC_ERR_UNSUPPORTED;
+    if (p->lo_grad && s->dev.n_lights != 1) return VRC_ERR_UNSUPPORTED;   // one light's phase per vertex
     if ((out->hit_prim != nullptr) != (out->hit_t != nullptr)) return VRC_ERR_INVALID;
     if (out->hit_prim && out->dbg_stride < nb * ns + 2) return VRC_ERR_INVALID;
     if (out->dbg_lit && (!out->hit_prim || out->dbg_shells < 1)) return VRC_ERR_INVALID;
@@ -1364,6 +1398,7 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     a.counter = s->d_counter;
     a.order = nullptr;
     a.parts = p->parts;
+    a.lo_grad = p->lo_grad ? 1 : 0;
     a.pre_ray = nullptr;
     a.pre_Lo = nullptr;
     a.pre_stride = (nb * ns + 2 + 31) & ~31;          // the largest ray set of the launch, whole warps
@@ -1390,6 +1425,8 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
         k_lpt_scatter<<<nbk, 256, 0, st>>>(d_n_bands, n, hist, s->d_order);
         a.order = s->d_order;
     }
+    if (a.lo_grad)   // compiled for the two default block shapes only
+        return nt == 384 ? launch_records<384, true>(s, a, smem, st) : launch_records<256, true>(s, a, smem, st);
     switch (nt) {
         case 128: return launch_records<128>(s, a, smem, st);
         case 384: return launch_records<384>(s, a, smem, st);
