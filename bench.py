@@ -56,14 +56,62 @@ def cpu_model() -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed region: through NVML
+    (the driver's libnvidia-ml, read-only queries) every 10 ms, so that a timed region of a few
+    tens of milliseconds still gets several samples; nvidia-smi every 200 ms if NVML cannot be
+    loaded."""
 
-    def __init__(self, index: int):
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index: int, period_s: float = 0.01):
         self.index = index
+        self.period = period_s
         self.proc = None
         self.lines = []
+        self.samples = []          # (sm MHz, max sm MHz, reason bits) from NVML
+        self.stop = threading.Event()
+        self.t = None
+
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(self.index), "uuid", None)
+            if u is not None:
+                uuid = "GPU-" + str(u)
+        except Exception:
+            uuid = None
+        if uuid is None or lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        return lib, h
+
+    def _poll(self, lib, h):
+        import ctypes
+        sm, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0 and        # NVML_CLOCK_SM
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    get_reasons(h, ctypes.byref(rs)) == 0):
+                self.samples.append((float(sm.value), float(mx.value), int(rs.value)))
+            self.stop.wait(self.period)
 
     def __enter__(self):
+        try:
+            lib, h = self._nvml_handle()
+            self.t = threading.Thread(target=self._poll, args=(lib, h), daemon=True)
+            self.t.start()
+            return self
+        except (OSError, AttributeError):
+            pass
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -82,14 +130,23 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        elif self.t is not None:
+            self.t.join(timeout=5)
 
     def summary(self):
+        if self.samples:
+            sm = [x[0] for x in self.samples]
+            reasons = sorted({nm for _, _, bits in self.samples for b, nm in self.REASONS.items() if bits & b})
+            return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(min(sm)),
+                    "sm_max_mhz": self.samples[-1][1], "reasons": reasons, "samples": len(sm),
+                    "source": f"NVML every {self.period * 1e3:.0f} ms"}
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
@@ -105,7 +162,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi every 200 ms"}
 
 
 def measured_peaks():
@@ -119,8 +176,8 @@ def measured_peaks():
 
 
 # DRAM bytes per record of k_records (the pre-pass rays it loads dominate), from one ncu
-# capture of a 1,024-record launch of the mid workload: (65.88 MB + 3.11 MB) / 1,024
-K_RECORDS_DRAM_BYTES_PER_RECORD = (65.877504e6 + 3.1104e6) / 1024
+# capture of a 1,024-record launch of the mid workload: (65.73 MB + 3.23 MB) / 1,024
+K_RECORDS_DRAM_BYTES_PER_RECORD = (65.729536e6 + 3.228928e6) / 1024
 
 
 def fp32_peak_tflops(sm_mhz: float = 2070.0, n_sm: int = 152) -> float:
@@ -361,9 +418,36 @@ def run_gpu(args, w, rank, world, local_rank):
             dbg = vrc.compute_records(scene, pos, rp, debug_hits=True)
             gpu_dbg = {k: v.cpu().numpy() for k, v in dbg.items() if k in ("L", "grad", "hess", "hit_prim", "hit_t",
                                                                             "dbg_lit")}
+        # after the records above were read back: these calls overwrite them
+        extra = None if args.no_lo_grad else {"lo_grad": lo_grad_rates(vrc, scene, pos, rp, rec, flush, stream)}
         line = report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h,
-                      kernel_ms, gpu_rec, gpu_dbg)
+                      kernel_ms, gpu_rec, gpu_dbg, extra)
     return line
+
+
+def lo_grad_rates(vrc, scene, pos, rp, rec, flush, stream, reps: int = 20) -> dict:
+    """compute_records alone with the lo_grad option (a medium vertex's radiance varying with x)
+    and without it, on the same records (CUDA events, L2 flushed before each call)."""
+    import dataclasses
+
+    import torch
+    out = {}
+    for name, p in (("off", rp), ("on", dataclasses.replace(rp, lo_grad=1))):
+        for _ in range(3):
+            vrc.compute_records(scene, pos, p, out=rec)
+        t = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            vrc.compute_records(scene, pos, p, out=rec)
+            b.record(stream)
+            t.append((a, b))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in t]))
+        out[name] = {"ms": ms, "records_per_s": pos.shape[0] / (ms * 1e-3)}
+    out["cost"] = out["on"]["ms"] / out["off"]["ms"]
+    return out
 
 
 def e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, flush):
@@ -399,7 +483,7 @@ def e2e_measure(args, w, vrc, scene, rp, pos_np, q_np, pos, q, rec, rgb, cnt, fl
 
 
 def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h, kernel_ms,
-           gpu_rec=None, gpu_dbg=None):
+           gpu_rec=None, gpu_dbg=None, extra=None):
     value = world * w.n_records / (ms * 1e-3)
     if True:
         clk = clocks.summary()
@@ -493,6 +577,8 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
                     "reference_noise_floor": c["reference_noise_floor"]}
             except Exception as ex:          # reported, not fatal to the line
                 line["learned_vs_plain"] = {"error": f"{type(ex).__name__}: {ex}"}
+        if extra:
+            line.update(extra)
         print(json.dumps(line), flush=True)
     return line
 
@@ -654,7 +740,10 @@ def run_mlp(args):
             "config": {"workload": "learned radius predictor: 256-64-64-1 GELU MLP, 1M rows; training batches of 4,096",
                        "l2": "flushed between timed passes (256 MB write)"},
             "roofline": {"kernel": "k_mlp_forward_tma (BF16 features)", "bound": "hbm", "achieved": fwd_gbs,
-                         "peak": hbm, "unit": "GB/s", "frac": fwd_gbs / hbm, "traffic": None,
+                         "peak": hbm, "unit": "GB/s", "frac": fwd_gbs / hbm,
+                         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1M-row launch
+                         "traffic": (537.16e6 + 7.06e6) * n / 1048576,
+                         "traffic_source": "ncu capture of one 1,048,576-row launch, scaled by rows",
                          "tensor_tflops": n * flop_row / (fwd_ms * 1e-3) / 1e12, "bf16_peak_tflops": bf16},
             "forward_fp32_features": {"kernel": "k_mlp_forward", "ms": fwd32_ms, "predictions_per_s": n / (fwd32_ms * 1e-3),
                                       "achieved_gbs": fwd32_gbs, "frac": fwd32_gbs / hbm},
@@ -928,7 +1017,7 @@ def run_render(args, w):
     base = res[f"learned_eps{rp.eps:g}"]
     line = {"metric": METRIC, "value": n_q / (base["frame_ms"] * 1e-3), "unit": "march points/s (whole frame)",
             "runs": res, "equal_error": equal,
-            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": "f32 (f64 eigen-solve)",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "dtype": DTYPE,
             "data": "synthetic", "config": {"workload": w.name, "scene_tris": w.scene.n_tris,
                                             "pixels": Wd * Hd, "march_steps": steps,
                                             "record_rays": rp.n_rays, "prepass_stride": 8},
@@ -955,6 +1044,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain placement comparison")
+    ap.add_argument("--no-lo-grad", action="store_true", help="skip the lo_grad record-option timing")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
     ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat", "mlp", "learned"],
