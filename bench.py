@@ -7,7 +7,10 @@ A step is one pass of the whole hot path over one batch of the mid workload
 `value` is records per second of the whole step; queries per second of the same
 step, per-phase rates, the roofline of the record kernel, the end-to-end rate
 through host buffers and the FP64 oracle timed on the host cores are reported in
-the same JSON line.
+the same JSON line.  After the timed region the line also carries the parity of
+all 4,096 records against the oracle, learned-vs-plain placement, the lo_grad
+option's cost and summaries of the other workloads (batching, 2D, MLP, render;
+each is also its own line with --workload).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs its own independent batch (weak scaling, no
@@ -419,10 +422,48 @@ def run_gpu(args, w, rank, world, local_rank):
             gpu_dbg = {k: v.cpu().numpy() for k, v in dbg.items() if k in ("L", "grad", "hess", "hit_prim", "hit_t",
                                                                             "dbg_lit")}
         # after the records above were read back: these calls overwrite them
-        extra = None if args.no_lo_grad else {"lo_grad": lo_grad_rates(vrc, scene, pos, rp, rec, flush, stream)}
+        extra = {}
+        if not args.no_lo_grad:
+            extra["lo_grad"] = lo_grad_rates(vrc, scene, pos, rp, rec, flush, stream)
+        if not args.no_extra:
+            extra["workloads"] = extra_workloads(args)
         line = report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st, e2e_s, h2d, d2h,
                       kernel_ms, gpu_rec, gpu_dbg, extra)
     return line
+
+
+def extra_workloads(args) -> dict:
+    """The other workloads' lines, run after the timed region of the default line and
+    summarised in it (each is also its own line with --workload): the 100k-record batching
+    launch, the 2D world, the learned predictor's kernels and the rendered frame with its
+    equal-error comparison against the FP64 crop.  A workload that fails is reported as an
+    error, not fatal to the line."""
+    from workloads import flat as flat2d
+    sub = argparse.Namespace(**{**vars(args), "steps": 5, "warmup": 3})
+    out = {}
+    jobs = (("batching", lambda: run_batching(sub, W.config3(), emit=False)),
+            ("flat", lambda: run_flat(sub, flat2d.flat_mid(), emit=False)),
+            ("mlp", lambda: run_mlp(sub, emit=False)),
+            ("render", lambda: run_render(sub, W.config5(), emit=False)))
+    keep = {"batching": ("value", "unit", "ms_per_step", "plain_ms", "graph_ms", "tuning", "primary_rays_per_s"),
+            "flat": ("value", "unit", "ms_per_step", "records_per_s_kernel", "queries_per_s_of_step"),
+            "mlp": ("value", "unit", "ms_per_step", "roofline", "forward_fp32_features", "train_rows_per_s"),
+            "render": ("value", "unit", "equal_error_measure", "fp64_crop", "equal_error",
+                       "reference_noise_floor_rel_rmse", "oracle_spot_check_max_err_over_tol")}
+    for name, job in jobs:
+        t0 = time.perf_counter()
+        try:
+            line = job()
+            d = {k: line.get(k) for k in keep[name]}
+            d["workload"] = line["config"]["workload"]
+            if name == "render":
+                d["runs"] = {k: {kk: v[kk] for kk in ("frame_ms", "records", "rel_rmse_fp64_crop", "rel_rmse")}
+                             for k, v in line["runs"].items()}
+            d["seconds"] = time.perf_counter() - t0
+            out[name] = d
+        except Exception as ex:
+            out[name] = {"error": f"{type(ex).__name__}: {ex}"}
+    return out
 
 
 def lo_grad_rates(vrc, scene, pos, rp, rec, flush, stream, reps: int = 20) -> dict:
@@ -583,7 +624,7 @@ def report(args, w, world, ms, rec_ms, q_ms, t_grid, clocks, n_cells, n_far, st,
     return line
 
 
-def run_batching(args, w):
+def run_batching(args, w, emit: bool = True):
     """Extra measurement (not the default line): the batching workload's records/s,
     plain launch vs CUDA-graph replay after autotuning."""
     import torch
@@ -621,10 +662,12 @@ def run_batching(args, w):
                        "primary_rays": rays, "l2": "scene 6 MB BVH; inputs 1.2 MB"},
             "plain_ms": res["plain"], "graph_ms": res["graph"], "tuning": best, "autotune_s": tune_s,
             "primary_rays_per_s": rays / (res["graph"] * 1e-3)}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_flat(args, w):
+def run_flat(args, w, emit: bool = True):
     """Extra measurement (not the default line): the 2D world's mid workload (4,096 records x
     512 directions, 161 segments) -- records/s of vrc2d_compute_records, queries/s through
     the record grid in the plane z = 0.5 (1M queries), and the 2D FP64 oracle's records/s on
@@ -672,10 +715,12 @@ def run_flat(args, w):
             "covered_fraction": float((cnt > 0).float().mean().item()),
             "cpu_baseline": {"value": n_cpu / cpu_s, "unit": "records/s", "cores": 1, "kind": "oracle",
                              "sample": f"{n_cpu} records of the workload, one thread"}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_mlp(args):
+def run_mlp(args, emit: bool = True):
     """Extra measurement (not the default line): the learned radius predictor's kernels.
     Inference: 1M feature rows -> log radius, from BF16 features brought in by tiled TMA
     copies (k_mlp_forward_tma: 516 B per row read and written) and from FP32 features
@@ -749,7 +794,9 @@ def run_mlp(args):
                                       "achieved_gbs": fwd32_gbs, "frac": fwd32_gbs / hbm},
             "train_step_ms": step_ms, "train_rows_per_s": bsz / (step_ms * 1e-3),
             "train_tflops": 3 * flop_row * bsz / (step_ms * 1e-3) / 1e12}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 3000) -> dict:
@@ -868,7 +915,7 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
                                       "rel_rmse": float(np.sqrt(np.mean((ref2 - ref) ** 2)) / np.mean(np.abs(ref)))}}
 
 
-def run_learned(args):
+def run_learned(args, emit: bool = True):
     """Extra measurement: the learned-vs-plain comparison (learned_comparison) as its own line."""
     from paper_1805_09258_gb300 import build as vbuild
     vbuild.build()
@@ -878,10 +925,12 @@ def run_learned(args):
             "unit": "candidate points covered/s (learned one-shot placement)", "n_gpus": 1, "steps": 1, "warmup": 1,
             "higher_is_better": True, "dtype": "f32 records, bf16 predictor", "data": "synthetic",
             "config": {"workload": cmp_["workload"]}, **{k: v for k, v in cmp_.items() if k != "workload"}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_render(args, w):
+def run_render(args, w, emit: bool = True):
     """Extra measurement (not the default line): one 1920x1080 frame of the render-shaped
     workload, plain vs learned placement (and ellipsoidal / split-cache variants), each at
     several error tolerances, with the frame's error measured on 16 crops of 16x16 pixels
@@ -944,11 +993,11 @@ def run_render(args, w):
 
     floor = rel_rmse(ref2)
     # the FP64 reference: the frame's central 64 x 64 pixels with a full oracle record at
-    # every march point (oracle/render.py; computed once into the oracle's cache directory)
+    # every march point (oracle/render.py: its pixels are stored next to it, the full crop in
+    # the oracle's cache directory)
     import oracle.render as orender
-    crop_path = orender.render_crop_path(64)
     fp64 = None
-    if os.path.exists(crop_path):
+    if orender.crop_available(64):
         fp64 = orender.central_crop(64)
         cx0, cy0, cs = int(fp64["x0"]), int(fp64["y0"]), int(fp64["w"])
         fp_img = fp64["img"].reshape(-1, 3)
@@ -1032,7 +1081,9 @@ def run_render(args, w):
             "light_pixel": [lx, ly],
             "reference_noise_floor_rel_rmse": floor,
             "oracle_spot_check_max_err_over_tol": spot}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -1045,6 +1096,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain placement comparison")
     ap.add_argument("--no-lo-grad", action="store_true", help="skip the lo_grad record-option timing")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batching, 2D, MLP and render workloads' summaries in the default line")
     ap.add_argument("--records", type=int, default=0, help="smaller record batch (profiling captures only)")
     ap.add_argument("--queries", type=int, default=0, help="smaller query batch (profiling captures only)")
     ap.add_argument("--workload", default="mid", choices=["mid", "batching", "render", "flat", "mlp", "learned"],

@@ -13,6 +13,9 @@ x = (2 (px + 1/2) / W - 1) tan(vfov / 2) W / H and y = (1 - 2 (py + 1/2) / H) ta
 
 Usage (computes and caches the central crop of the render workload):
     python -m oracle.render [--size 64] [--threads N] [--out PATH]
+Besides the full cache (per-march-point radiance, in the git-ignored cache directory) it writes
+the composited pixels alone next to this file (render_crop_<size>.npz): the expected image that
+the benchmark's equal-error comparison reads when the cache is absent.
 """
 from __future__ import annotations
 
@@ -113,6 +116,17 @@ def render_crop_path(size: int = 64) -> str:
     return os.path.join(CACHE_DIR, f"render_crop_{size}.npz")
 
 
+def render_crop_pixels_path(size: int = 64) -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), f"render_crop_{size}.npz")
+
+
+PIXEL_KEYS = ("img", "valid", "x0", "y0", "w", "h", "steps", "seconds")
+
+
+def crop_available(size: int = 64) -> bool:
+    return os.path.exists(render_crop_path(size)) or os.path.exists(render_crop_pixels_path(size))
+
+
 def central_crop(size: int = 64, n_threads: int = 0, out: str = None, verbose: bool = False) -> dict:
     """The render workload's central size x size pixels (cached); record ids are the march
     points' indices over the whole crop (pixel rows in order, `steps` points per pixel)."""
@@ -120,9 +134,10 @@ def central_crop(size: int = 64, n_threads: int = 0, out: str = None, verbose: b
     w = W.config5()
     ex = w.extra
     path = out or render_crop_path(size)
-    if os.path.exists(path):
-        z = np.load(path)
-        return {k: z[k] for k in z.files}
+    for p in (path, render_crop_pixels_path(size)):
+        if os.path.exists(p):
+            z = np.load(p)
+            return {k: z[k] for k in z.files}
     cam = camera(ex["camera"], ex["forward"], ex["vfov_deg"], ex["width"], ex["height"])
     x0, y0 = (ex["width"] - size) // 2, (ex["height"] - size) // 2
     t0 = time.time()
@@ -148,9 +163,16 @@ def central_crop(size: int = 64, n_threads: int = 0, out: str = None, verbose: b
     os.makedirs(os.path.dirname(path), exist_ok=True)
     np.savez_compressed(path + ".tmp.npz", **res)
     os.replace(path + ".tmp.npz", path)
+    write_pixels(res, render_crop_pixels_path(size))
     for r0 in range(0, size, rows):
         os.remove(path + f".rows{r0}.npz")
     return res
+
+
+def write_pixels(res: dict, path: str) -> None:
+    """The composited crop alone (the pixels, their mask and the crop's placement)."""
+    np.savez_compressed(path + ".tmp.npz", **{k: np.asarray(res[k]) for k in PIXEL_KEYS})
+    os.replace(path + ".tmp.npz", path)
 
 
 if __name__ == "__main__":
@@ -158,5 +180,11 @@ if __name__ == "__main__":
     ap.add_argument("--size", type=int, default=64)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--pixels-only", action="store_true",
+                    help="rewrite the pixel file from an existing full cache, without recomputing")
     a = ap.parse_args()
-    central_crop(a.size, a.threads, a.out, verbose=True)
+    if a.pixels_only:
+        z = np.load(a.out or render_crop_path(a.size))
+        write_pixels({k: z[k] for k in z.files}, render_crop_pixels_path(a.size))
+    else:
+        central_crop(a.size, a.threads, a.out, verbose=True)

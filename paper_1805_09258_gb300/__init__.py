@@ -212,7 +212,7 @@ class Scene:
         t = RecordTuning()
         _check(load_library().vrc_get_record_tuning(self.handle, C.byref(t)), "vrc_get_record_tuning")
         return dict(threads=t.threads, chunk_bands=t.chunk_bands, blocks_per_sm=t.blocks_per_sm,
-                    shadow_bvh=t.shadow_bvh)
+                    shadow_bvh=t.shadow_bvh, no_prepass=t.no_prepass)
 
     def __del__(self):
         try:

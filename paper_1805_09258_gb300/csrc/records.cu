@@ -1356,6 +1356,8 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     if (p->parts < 0 || p->parts > 2) return VRC_ERR_INVALID;
     if (nb > 256 || ns > 512) return VRC_ERR_UNSUPPORTED;
     if (p->lo_grad && s->dev.n_lights != 1) return VRC_ERR_UNSUPPORTED;   // one light's phase per vertex
+    if (p->lo_grad && s->tuning.threads != 0 && s->tuning.threads != 256 && s->tuning.threads != 384)
+        return VRC_ERR_UNSUPPORTED;                     // compiled for the two default block shapes
     if ((out->hit_prim != nullptr) != (out->hit_t != nullptr)) return VRC_ERR_INVALID;
     if (out->hit_prim && out->dbg_stride < nb * ns + 2) return VRC_ERR_INVALID;
     if (out->dbg_lit && (!out->hit_prim || out->dbg_shells < 1)) return VRC_ERR_INVALID;

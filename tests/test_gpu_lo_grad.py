@@ -76,3 +76,24 @@ def test_more_than_one_light_is_refused(vrc):
     w.scene.lights = list(w.scene.lights) + [PointLight((0.2, 0.8, 0.7), (0.5, 0.5, 0.5))]
     with pytest.raises(vrc.VrcError, match="unsupported"):
         _run(vrc, w, replace(w.params, lo_grad=1), w.positions(8))
+
+
+def test_other_block_shapes_are_refused_and_256_threads_agree(vrc):
+    """The option's kernel is built for 256- and 384-thread blocks: other explicit launch
+    shapes are refused; 256 threads in band chunks give the default launch's records up to
+    the order of the sums."""
+    w = W.config1()
+    rp = replace(w.params, lo_grad=1)
+    pos = torch.from_numpy(w.positions()).cuda()
+    s = vrc.Scene.from_workload(w.scene)
+    ref = to_np(vrc.compute_records(s, pos, rp))
+    for t in (128, 512):
+        s.set_tuning(threads=t)
+        with pytest.raises(vrc.VrcError, match="unsupported"):
+            vrc.compute_records(s, pos, rp)
+    s.set_tuning(threads=256, chunk_bands=4)
+    g = to_np(vrc.compute_records(s, pos, rp))
+    torch.cuda.synchronize()
+    for k in ("L", "grad", "hess"):
+        scale = np.abs(ref[k]).max(axis=1, keepdims=True) + 1e-30
+        assert np.all(np.abs(g[k] - ref[k]) <= 1e-4 * scale), k

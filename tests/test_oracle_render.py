@@ -66,3 +66,25 @@ def test_march_weights_and_first_hit():
     exact = sig_s * (1.0 - np.exp(-sig_t * length)) / sig_t
     ds = length / steps
     assert np.all(np.abs(wts.sum(1) - exact) <= sig_s * sig_t ** 2 * length * ds ** 2 / 24 * 1.01 + 1e-15)
+
+
+def test_stored_crop_pixels_are_the_oracles():
+    """The stored FP64 crop (oracle/render_crop_64.npz, written by `python -m oracle.render`)
+    holds the oracle's own pixels: two of them recomputed here, with the record ids the crop
+    gives their march points, match to rounding."""
+    import os
+
+    import workloads as W
+    path = R.render_crop_pixels_path(64)
+    assert os.path.exists(path)
+    z = np.load(path)
+    w = W.config5()
+    ex = w.extra
+    cam = R.camera(ex["camera"], ex["forward"], ex["vfov_deg"], ex["width"], ex["height"])
+    size, steps = int(z["w"]), int(z["steps"])
+    assert (int(z["x0"]), int(z["y0"])) == ((ex["width"] - size) // 2, (ex["height"] - size) // 2)
+    for cx, cy in ((5, 9), (40, 62)):
+        r0 = cy - cy % 4                     # the crop is computed in blocks of 4 pixel rows
+        base = r0 * size * steps + ((cy - r0) * size + cx) * steps
+        one = R.crop(w.scene, w.params, cam, int(z["x0"]) + cx, int(z["y0"]) + cy, 1, 1, steps, rec_base=base)
+        assert np.allclose(one["img"][0, 0], z["img"][cy, cx], rtol=1e-12, atol=1e-15)
