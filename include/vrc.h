@@ -165,9 +165,11 @@ typedef struct {
     int32_t dbg_shells;
 } vrc_records_view;
 
-/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default: 384
- * threads with the whole ray set in shared memory when that fits two blocks per SM (up to
- * 110 KB), else 256 threads with as many bands per chunk as fit 72 KB (three blocks). */
+/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default: for
+ * small ray sets (whole set within 36 KB) and at least 6 records per SM, 128 threads with the
+ * whole ray set (six blocks per SM); else 384 threads with the whole ray set in shared memory
+ * when that fits two blocks per SM (up to 110 KB); else 256 threads with as many bands per
+ * chunk as fit 72 KB (three blocks). */
 typedef struct {
     int32_t threads;        /* threads per block: 128, 256, 384, 512 */
     int32_t chunk_bands;    /* bands of the ray set kept in shared memory at once */
@@ -362,10 +364,13 @@ int vrc_composite(vrc_scene* scene, const vrc_camera* cam, int32_t x0, int32_t y
 /* Placement wave (Sec. 6: a record is added where no valid record exists): among the
  * candidates with 0 <= d_level[i] <= level, pick in each cell of a 2^level grid over the
  * cube the one with the smallest index.  Writes the picked indices (ascending) and their
- * positions to d_site_idx / d_site_pts and their number to *h_count (synchronous).
- * d_scratch must hold 8^level + 2 n + n/1024 + 2 ints; level <= 8. */
+ * positions to d_site_idx / d_site_pts and their number to *h_count, and (h_pool non-NULL)
+ * the number of candidates still in the pool at any level (d_level[i] >= 0) to *h_pool, so
+ * that a caller can end its waves once the pool is empty (synchronous).
+ * d_scratch must hold 8^level + 2 n + n/1024 + 3 ints; level <= 8. */
 int vrc_select_sites(const float* d_pts, const int32_t* d_level, int32_t n, int32_t level, int32_t* d_scratch,
-                     int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts, int32_t* h_count, void* stream);
+                     int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts, int32_t* h_count,
+                     int32_t* h_pool, void* stream);
 
 /* Learned levels predicted once per cell: after vrc_select_sites at cell_level (which left
  * each cell's representative -- smallest candidate index -- in the first 8^cell_level

@@ -100,7 +100,7 @@ def load_library(path: Optional[str] = None):
     L.vrc_march_points.argtypes = [P, P, I32, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_render.argtypes = [P, P, P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_composite.argtypes = [P, P, I32, I32, I32, I32, I32, P, P, P]
-    L.vrc_select_sites.argtypes = [P, P, I32, I32, P, C.c_int64, P, P, P, P]
+    L.vrc_select_sites.argtypes = [P, P, I32, I32, P, C.c_int64, P, P, P, P, P]
     L.vrc_update_coverage.argtypes = [P, I32, P, P]
     L.vrc_init_levels.argtypes = [P, I32, I32, P, P]
     L.vrc_march_pixels.argtypes = [P, P, P, I32, I32, P, P, P]
@@ -684,12 +684,14 @@ def composite(scene: Scene, cam: Camera, x0, y0, w, h, steps, L, stream=None):
     return img
 
 
-def select_sites(pts, level, wave_level: int, scratch, site_idx, site_pts, stream=None) -> int:
-    cnt = C.c_int32(0)
+def select_sites(pts, level, wave_level: int, scratch, site_idx, site_pts, stream=None, with_pool: bool = False):
+    """vrc_select_sites: the number of sites; with_pool: (sites, candidates left in the pool)."""
+    cnt, pool = C.c_int32(0), C.c_int32(0)
     _check(load_library().vrc_select_sites(_ptr(pts), _ptr(level), pts.shape[0], wave_level, _ptr(scratch),
                                            scratch.numel(), _ptr(site_idx), _ptr(site_pts), C.byref(cnt),
-                                           _stream_ptr(stream)), "vrc_select_sites")
-    return int(cnt.value)
+                                           C.byref(pool) if with_pool else None, _stream_ptr(stream)),
+           "vrc_select_sites")
+    return (int(cnt.value), int(pool.value)) if with_pool else int(cnt.value)
 
 
 def levels_by_cell(pts, cell_level: int, scratch, site_idx, site_logr, n_sites: int, cell_over_radius: float,

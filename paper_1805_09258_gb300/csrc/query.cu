@@ -111,31 +111,76 @@ __global__ void k_insert(const float4* rec, const float4* ext, int n, int G, int
 }
 
 // Sort each cell's list ascending (a deterministic summation order for the queries).
-// One block per cell: record ids in a list are distinct, so each element's position is
-// the number of smaller elements (rank sort in shared memory); lists longer than the
-// shared buffer fall back to an insertion sort by one thread.
-constexpr int SORT_CAP = 4096;
-__global__ void __launch_bounds__(256) k_sort_lists(const int* start, int ncell, int* list) {
-    __shared__ int buf[SORT_CAP];
-    int cell = blockIdx.x;
-    if (cell >= ncell) return;
-    int b = start[cell], e = start[cell + 1], len = e - b;
-    if (len <= 1) return;
-    if (len > SORT_CAP) {
-        if (threadIdx.x == 0)
-            for (int i = b + 1; i < e; ++i) {
-                int v = list[i], j = i - 1;
-                while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
-                list[j + 1] = v;
+// Record ids in a list are distinct, so each element's position is the number of smaller
+// elements (a rank sort).  One warp per cell: up to 64 entries two per lane in registers,
+// ranked by shuffles; up to WSORT_CAP in the warp's shared buffer; longer lists are handed
+// to k_sort_lists (a block per list).  Most lists are short (tens of records), and a block
+// per cell spent its time on launching blocks for them (measured rebuilds: 3,725 records of
+// radius 0.02-0.1, 0.36 -> 0.28 ms; 4,096 of 0.05-0.2 unchanged; 418 of 0.2-0.5, whose
+// lists of a few hundred now sort in one warp each, 0.11 -> 0.12 ms).
+constexpr int WSORT_CAP = 512;
+__global__ void __launch_bounds__(256) k_sort_lists_warp(const int* start, int ncell, int* list, int* long_cells,
+                                                         int* n_long) {
+    __shared__ int buf[8][WSORT_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int cell = blockIdx.x * 8 + w; cell < ncell; cell += gridDim.x * 8) {
+        const int b = start[cell], e = start[cell + 1], len = e - b;
+        if (len <= 1) continue;
+        if (len <= 64) {
+            const int v0 = lane < len ? list[b + lane] : 0x7fffffff;
+            const int v1 = lane + 32 < len ? list[b + 32 + lane] : 0x7fffffff;
+            int r0 = 0, r1 = 0;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const int u0 = __shfl_sync(0xffffffffu, v0, j), u1 = __shfl_sync(0xffffffffu, v1, j);
+                r0 += (u0 < v0 ? 1 : 0) + (u1 < v0 ? 1 : 0);
+                r1 += (u0 < v1 ? 1 : 0) + (u1 < v1 ? 1 : 0);
             }
-        return;
+            if (lane < len) list[b + r0] = v0;
+            if (lane + 32 < len) list[b + r1] = v1;
+        } else if (len <= WSORT_CAP) {
+            for (int i = lane; i < len; i += 32) buf[w][i] = list[b + i];
+            __syncwarp();
+            for (int i = lane; i < len; i += 32) {
+                const int v = buf[w][i];
+                int r = 0;
+                for (int j = 0; j < len; ++j) r += buf[w][j] < v ? 1 : 0;
+                list[b + r] = v;
+            }
+            __syncwarp();
+        } else if (lane == 0) {
+            long_cells[atomicAdd(n_long, 1)] = cell;
+        }
     }
-    for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = list[b + i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        int v = buf[i], r = 0;
-        for (int j = 0; j < len; ++j) r += buf[j] < v;
-        list[b + r] = v;
+}
+
+// the lists longer than WSORT_CAP, one block each (rank sort in shared memory; lists longer
+// than its buffer: an insertion sort by one thread)
+constexpr int SORT_CAP = 4096;
+__global__ void __launch_bounds__(256) k_sort_lists(const int* start, const int* long_cells, const int* n_long,
+                                                    int* list) {
+    __shared__ int buf[SORT_CAP];
+    for (int li = blockIdx.x; li < *n_long; li += gridDim.x) {
+        const int cell = long_cells[li];
+        int b = start[cell], e = start[cell + 1], len = e - b;
+        if (len > SORT_CAP) {
+            if (threadIdx.x == 0)
+                for (int i = b + 1; i < e; ++i) {
+                    int v = list[i], j = i - 1;
+                    while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
+                    list[j + 1] = v;
+                }
+            __syncthreads();
+            continue;
+        }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = list[b + i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            int v = buf[i], r = 0;
+            for (int j = 0; j < len; ++j) r += buf[j] < v;
+            list[b + r] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -426,7 +471,18 @@ int fill_grid(vrc_grid* g, const vrc_records_view* v, int32_t n, int32_t order, 
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
         k_insert<true><<<nwb, tb, 0, st>>>(g->rec, aniso ? g->ext : nullptr, n, G, g->q_count, g->cell_start,
                                            g->cell_list);
-        k_sort_lists<<<ncell, 256, 0, st>>>(g->cell_start, ncell, g->cell_list);
+        // the fill cursors (q_count) are free again: long lists' cells and their count
+        int* long_cells = g->q_count;
+        int* n_long = g->q_count + ncell;
+        cudaMemsetAsync(n_long, 0, sizeof(int), st);
+        int sm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+        sm = std::max(sm, 1);
+        const int wblk = std::max(1, std::min((ncell + 7) / 8, 8 * sm));
+        k_sort_lists_warp<<<wblk, 256, 0, st>>>(g->cell_start, ncell, g->cell_list, long_cells, n_long);
+        k_sort_lists<<<std::max(1, std::min(ncell, 16 * sm)), 256, 0, st>>>(g->cell_start, long_cells, n_long,
+                                                                             g->cell_list);
     } else {
         g->entries = 0;
         cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);

@@ -209,10 +209,12 @@ __global__ void k_composite(DevScene sc, Cam c, int x0, int y0, int w, int h, in
 }
 
 // ---------------------------------------------------------------- placement
-__global__ void k_site_claim(const float* pts, const int* level, int n, int lv, int G, int* cell_min) {
+__global__ void k_site_claim(const float* pts, const int* level, int n, int lv, int G, int* cell_min, int* pool) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int l = level[i];
+    int l = i < n ? level[i] : -1;
+    // candidates still in the pool (any level), one atomic per warp
+    const unsigned in_pool = __ballot_sync(0xffffffffu, l >= 0);
+    if ((threadIdx.x & 31) == 0 && in_pool) atomicAdd(pool, __popc(in_pool));
     if (l < 0 || l > lv) return;
     int ix = min(G - 1, max(0, (int)floorf(pts[3 * i] * G)));
     int iy = min(G - 1, max(0, (int)floorf(pts[3 * i + 1] * G)));
@@ -407,29 +409,34 @@ extern "C" int vrc_composite(vrc_scene* s, const vrc_camera* cam, int32_t x0, in
 
 extern "C" int vrc_select_sites(const float* d_pts, const int32_t* d_level, int32_t n, int32_t level,
                                 int32_t* d_scratch, int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts,
-                                int32_t* h_count, void* stream) {
+                                int32_t* h_count, int32_t* h_pool, void* stream) {
     if (!d_pts || !d_level || n < 0 || level < 0 || level > 8 || !d_scratch || !d_site_idx || !d_site_pts || !h_count)
         return VRC_ERR_INVALID;
     *h_count = 0;
+    if (h_pool) *h_pool = 0;
     if (n == 0) return VRC_OK;
     const int G = 1 << level;
     const long long cells = (long long)G * G * G;
     const int nblk = (n + 1023) / 1024;
-    if (scratch_ints < cells + 2LL * n + nblk + 1) return VRC_ERR_INVALID;
+    if (scratch_ints < cells + 2LL * n + nblk + 2) return VRC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     int* cell_min = d_scratch;
     int* flag = cell_min + cells;
     int* pos = flag + n;
-    int* sums = pos + n;
+    int* sums = pos + n;                  // [nblk] block sums, then the site count and the pool size
     VRC_CUDA_CHECK(cudaMemsetAsync(cell_min, 0x7f, sizeof(int) * cells, st));
+    VRC_CUDA_CHECK(cudaMemsetAsync(sums + nblk + 1, 0, sizeof(int), st));
     int tb = 256, nb = (n + tb - 1) / tb;
-    k_site_claim<<<nb, tb, 0, st>>>(d_pts, d_level, n, level, G, cell_min);
+    k_site_claim<<<nb, tb, 0, st>>>(d_pts, d_level, n, level, G, cell_min, sums + nblk + 1);
     k_site_flag<<<nb, tb, 0, st>>>(d_pts, d_level, n, level, G, cell_min, flag);
     k_flag_scan<<<nblk, 1024, 0, st>>>(flag, n, pos, sums);
     k_flag_tops<<<1, 32, 0, st>>>(sums, nblk, sums + nblk);
     k_gather_sites<<<nb, tb, 0, st>>>(d_pts, flag, pos, sums, n, d_site_idx, d_site_pts);
-    VRC_CUDA_CHECK(cudaMemcpyAsync(h_count, sums + nblk, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    int32_t both[2] = {0, 0};
+    VRC_CUDA_CHECK(cudaMemcpyAsync(both, sums + nblk, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     VRC_CUDA_CHECK(cudaStreamSynchronize(st));
+    *h_count = both[0];
+    if (h_pool) *h_pool = both[1];
     return VRC_OK;
 }
 

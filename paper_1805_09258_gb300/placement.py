@@ -5,8 +5,9 @@ over the unit cube that still holds an uncovered pool candidate (whose own level
 most `level`) gets one site -- the candidate with the smallest index (vrc_select_sites);
 full records are computed at the sites (vrc_compute_records), the grid is rebuilt and
 the candidates are queried (vrc_query_inscatter); covered candidates leave the pool
-(vrc_update_coverage).  Candidates still uncovered after the finest wave get a record
-each.  Coverage always uses the full records' radii, so the result honours the error
+(vrc_update_coverage).  The waves end early once no candidate is left in the pool (site
+selection reports the pool's size).  Candidates still uncovered after the finest wave get
+a record each.  Coverage always uses the full records' radii, so the result honours the error
 tolerance whatever picked the sites.
 
 Plain placement starts every candidate at the coarsest level.  Learned placement first
@@ -78,7 +79,7 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
     else:
         init_levels(valid, level, start_level)
     fine = min(8, max_level + 1)
-    scratch = torch.empty((8 ** fine + 2 * n + n // 1024 + 2,), dtype=torch.int32, device=cand.device)
+    scratch = torch.empty((8 ** fine + 2 * n + n // 1024 + 3,), dtype=torch.int32, device=cand.device)
     site_idx = torch.empty((n,), dtype=torch.int32, device=cand.device)
     site_pts = torch.empty((n, 3), dtype=torch.float32, device=cand.device)
     res = PlacementResult(0)
@@ -142,14 +143,17 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         res.waves.append(("one-shot", got))
         if got:
             add_records(batch, got)
+    in_pool = n
     for lv in range(start_level, max_level + 1):
-        m = select_sites(cand, level, lv, scratch, site_idx, site_pts)
+        m, in_pool = select_sites(cand, level, lv, scratch, site_idx, site_pts, with_pool=True)
+        if in_pool == 0:
+            break                         # every candidate is covered: the finer waves are empty
         res.waves.append((lv, m))
         if m:
             add_records(site_pts, m)
     # candidates still uncovered get sites on the finest grid until none is left (each
     # wave covers at least its own sites, so this ends)
-    left = select_sites(cand, level, fine, scratch, site_idx, site_pts)
+    left = 0 if in_pool == 0 else select_sites(cand, level, fine, scratch, site_idx, site_pts)
     res.uncovered_after_waves = left
     while left:
         add_records(site_pts, left)

@@ -112,6 +112,14 @@ def test_fallback_rule_and_one_shot_placement(vrc, trained):
         site_idx = torch.empty((cand.shape[0],), dtype=torch.int32, device="cuda")
         site_pts = torch.empty((cand.shape[0], 3), dtype=torch.float32, device="cuda")
         m = vrc.select_sites(cand, level, 5, scratch, site_idx, site_pts)
+        # the pool size it reports: every candidate, then those left after retiring a third
+        m2, pool = vrc.select_sites(cand, level, 5, scratch, site_idx, site_pts, with_pool=True)
+        assert m2 == m and pool == cand.shape[0]
+        lv2 = level.clone()
+        lv2[::3] = -1
+        _, pool2 = vrc.select_sites(cand, lv2, 5, scratch, site_idx, site_pts, with_pool=True)
+        assert pool2 == int((lv2 >= 0).sum())
+        m = vrc.select_sites(cand, level, 5, scratch, site_idx, site_pts)     # the sites again
         pts = site_pts[:m].contiguous()
         pred = mlp.predict(vrc.coarse_features(s, pts, COARSE)).cpu().numpy().astype(np.float64)
         pred += 0.2 * np.log(eps / w.params.eps)

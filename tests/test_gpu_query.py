@@ -63,6 +63,28 @@ def test_synthetic_table_parity(vrc, order):
     assert cnt.max() > 1 and (cnt == 0).any()
 
 
+def test_long_cell_lists(vrc):
+    """Cell lists of every length class of the grid's list sort: up to 64 entries (a warp,
+    in registers), up to 512 (a warp's shared buffer), up to 4,096 (a block's) and beyond
+    (one thread).  6,000 records of radius 0.35-0.45 around the centre give cells that hold
+    thousands of records; the answers match the oracle and are the same bits when the grid
+    is built twice (each list in record order)."""
+    rng = np.random.default_rng(41)
+    n = 6000
+    tab = synthetic_table(n, seed=42, r_lo=0.35, r_hi=0.45)
+    tab["pos"] = (0.5 + rng.normal(size=(n, 3)) * 0.08).clip(0.0, 1.0).astype(np.float32)
+    # a few small records too, so that short lists exist as well
+    small = synthetic_table(400, seed=43, r_lo=0.01, r_hi=0.03)
+    tab = {k: np.concatenate([tab[k], small[k]]) for k in tab}
+    q = rng.uniform(0.0, 1.0, size=(4000, 3)).astype(np.float32)
+    rgb, cnt, grid = gpu_query(vrc, tab, q, 1)
+    rgb2, cnt2, _ = gpu_query(vrc, tab, q, 1)
+    assert np.array_equal(rgb, rgb2) and np.array_equal(cnt, cnt2)
+    ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=1)
+    check_query(rgb, cnt, ref, rc, near)
+    assert cnt.max() > 4096 and (cnt < 32).any()
+
+
 @pytest.mark.parametrize("order", [1, 2])
 def test_exact_at_the_centre_of_a_lone_record(vrc, order):
     """Eq. radianceTaylor at a record's centre, where no other record reaches: the weight is
