@@ -807,8 +807,8 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
     and split 80/10/10 (train / validation / test; the held-out errors are reported).
     Placement runs on a held-out scene (seed 41): 60,000 candidate points covered by plain
     waves, learned waves and learned one-shot placement (every predicted level's sites in
-    one batched launch, then plain repair waves), with predictions on a 2^5 or a 2^4 grid of
-    cells (the _p4 runs), each at 1, 1/10, 1/100 and 1/1000 of the
+    one batched launch, then plain repair waves), with predictions on a 2^5, 2^4 or 2^3 grid
+    of cells (the _p4 and _p3 runs), each at 1, 1/10, 1/100 and 1/1000 of the
     workload's tolerance, with the predictor's radius carried to each tolerance and checked
     against the coarse record (vrc_mlp_fallback).  Error: per-point relative luminance
     error at 619 held-out candidates against a 64x128-ray record there (mean, median, 90th
@@ -863,8 +863,8 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
         return float(np.sqrt(np.mean((L - ref) ** 2)) / np.mean(np.abs(ref)))
 
     eps0 = w.params.eps
-    # the prediction grid: one prediction per cell of a 2^5 grid (about 25k sites here) or of
-    # a 2^4 grid (about 4k: a sixth of the coarse records and features)
+    # the prediction grid: one prediction per cell of a 2^5 grid (about 25k sites here), of a
+    # 2^4 grid (about 4k: a sixth of the coarse records and features) or of a 2^3 grid (512)
     variants = (("plain", {}),
                 ("learned", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0)),
                 ("learned_one_shot", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
@@ -872,7 +872,11 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
                 ("learned_p4", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
                                     predict_level=4)),
                 ("learned_one_shot_p4", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
-                                             predict_level=4, one_shot=True)))
+                                             predict_level=4, one_shot=True)),
+                ("learned_p3", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
+                                    predict_level=3)),
+                ("learned_one_shot_p3", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
+                                             predict_level=3, one_shot=True)))
     res = {}
     # the tolerance bounds the error integrated over a record's ball (Eq. radiusAniso3D), so
     # the per-point error falls slowly with it (the radius goes as its fifth root)
@@ -881,7 +885,12 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
         for name, kw in variants:
             placement.place(s, rp, cand, **kw)                     # warm-up
             torch.cuda.synchronize()
-            r = placement.place(s, rp, cand, **kw)
+            # placement time: the median of five runs (each a few milliseconds)
+            times = []
+            for _ in range(5):
+                r = placement.place(s, rp, cand, **kw)
+                times.append(r.seconds)
+            r.seconds = float(np.median(times))
             rgb, cnt = vrc.query_inscatter(r.grid, q)
             L = rgb.cpu().numpy().astype(np.float64)
             e = rel_err(L)

@@ -112,12 +112,14 @@ __global__ void k_insert(const float4* rec, const float4* ext, int n, int G, int
 
 // Sort each cell's list ascending (a deterministic summation order for the queries).
 // Record ids in a list are distinct, so each element's position is the number of smaller
-// elements (a rank sort).  One warp per cell: up to 64 entries two per lane in registers,
-// ranked by shuffles; up to WSORT_CAP in the warp's shared buffer; longer lists are handed
-// to k_sort_lists (a block per list).  Most lists are short (tens of records), and a block
-// per cell spent its time on launching blocks for them (measured rebuilds: 3,725 records of
-// radius 0.02-0.1, 0.36 -> 0.28 ms; 4,096 of 0.05-0.2 unchanged; 418 of 0.2-0.5, whose
-// lists of a few hundred now sort in one warp each, 0.11 -> 0.12 ms).
+// elements (a rank sort).  Grids of up to WARP_SORT_CELLS cells: one block per cell
+// (k_sort_cells).  Finer grids (small radii, placement's fine waves at 64^3 cells): one warp
+// per cell, up to 64 entries two per lane in registers, ranked by shuffles, up to WSORT_CAP
+// in the warp's shared buffer, longer lists handed to k_sort_lists (a block per list); a
+// block per cell there spent its time on launching blocks for lists of a few tens
+// (measured rebuilds: 3,725 records of radius 0.02-0.1, 0.36 -> 0.28 ms; on the benchmark's
+// grid, 4,096 records, the block per cell stays 10 us faster).
+constexpr int WARP_SORT_CELLS = 1 << 17;
 constexpr int WSORT_CAP = 512;
 __global__ void __launch_bounds__(256) k_sort_lists_warp(const int* start, int ncell, int* list, int* long_cells,
                                                          int* n_long) {
@@ -154,9 +156,35 @@ __global__ void __launch_bounds__(256) k_sort_lists_warp(const int* start, int n
     }
 }
 
-// the lists longer than WSORT_CAP, one block each (rank sort in shared memory; lists longer
-// than its buffer: an insertion sort by one thread)
 constexpr int SORT_CAP = 4096;
+
+// one block per cell: rank sort in shared memory; lists longer than its buffer: an
+// insertion sort by one thread
+__global__ void __launch_bounds__(256) k_sort_cells(const int* start, int ncell, int* list) {
+    __shared__ int buf[SORT_CAP];
+    int cell = blockIdx.x;
+    if (cell >= ncell) return;
+    int b = start[cell], e = start[cell + 1], len = e - b;
+    if (len <= 1) return;
+    if (len > SORT_CAP) {
+        if (threadIdx.x == 0)
+            for (int i = b + 1; i < e; ++i) {
+                int v = list[i], j = i - 1;
+                while (j >= b && list[j] > v) { list[j + 1] = list[j]; --j; }
+                list[j + 1] = v;
+            }
+        return;
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = list[b + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        int v = buf[i], r = 0;
+        for (int j = 0; j < len; ++j) r += buf[j] < v;
+        list[b + r] = v;
+    }
+}
+
+// the lists longer than WSORT_CAP of a fine grid, one block each (as k_sort_cells)
 __global__ void __launch_bounds__(256) k_sort_lists(const int* start, const int* long_cells, const int* n_long,
                                                     int* list) {
     __shared__ int buf[SORT_CAP];
@@ -471,18 +499,22 @@ int fill_grid(vrc_grid* g, const vrc_records_view* v, int32_t n, int32_t order, 
         cudaMemsetAsync(g->q_count, 0, sizeof(int) * (ncell + 1), st);
         k_insert<true><<<nwb, tb, 0, st>>>(g->rec, aniso ? g->ext : nullptr, n, G, g->q_count, g->cell_start,
                                            g->cell_list);
-        // the fill cursors (q_count) are free again: long lists' cells and their count
-        int* long_cells = g->q_count;
-        int* n_long = g->q_count + ncell;
-        cudaMemsetAsync(n_long, 0, sizeof(int), st);
-        int sm = 0, dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
-        sm = std::max(sm, 1);
-        const int wblk = std::max(1, std::min((ncell + 7) / 8, 8 * sm));
-        k_sort_lists_warp<<<wblk, 256, 0, st>>>(g->cell_start, ncell, g->cell_list, long_cells, n_long);
-        k_sort_lists<<<std::max(1, std::min(ncell, 16 * sm)), 256, 0, st>>>(g->cell_start, long_cells, n_long,
-                                                                             g->cell_list);
+        if (ncell <= WARP_SORT_CELLS) {
+            k_sort_cells<<<ncell, 256, 0, st>>>(g->cell_start, ncell, g->cell_list);
+        } else {
+            // the fill cursors (q_count) are free again: long lists' cells and their count
+            int* long_cells = g->q_count;
+            int* n_long = g->q_count + ncell;
+            cudaMemsetAsync(n_long, 0, sizeof(int), st);
+            int sm = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+            sm = std::max(sm, 1);
+            const int wblk = std::max(1, std::min((ncell + 7) / 8, 8 * sm));
+            k_sort_lists_warp<<<wblk, 256, 0, st>>>(g->cell_start, ncell, g->cell_list, long_cells, n_long);
+            k_sort_lists<<<std::max(1, std::min(ncell, 16 * sm)), 256, 0, st>>>(g->cell_start, long_cells, n_long,
+                                                                                 g->cell_list);
+        }
     } else {
         g->entries = 0;
         cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), st);

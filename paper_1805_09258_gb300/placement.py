@@ -39,6 +39,17 @@ from . import (MLP, Grid, Scene, alloc_records, coarse_features, compute_records
                _torch)
 
 
+_SIDE = {}
+
+
+def _side_stream(torch, device):
+    """One second stream per device, kept for the process (created once)."""
+    key = torch.device(device).index
+    if key not in _SIDE:
+        _SIDE[key] = torch.cuda.Stream(device=device)
+    return _SIDE[key]
+
+
 @dataclass
 class PlacementResult:
     n_records: int
@@ -90,15 +101,25 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         m = select_sites(cand, level, predict_level, scratch, site_idx, site_pts)
         if m:
             pts = site_pts[:m].contiguous()
+            main = torch.cuda.current_stream()
+            rc = None
+            if fallback:
+                # the coarse ray set's own record at the placement's tolerance, on a second
+                # stream while the features and the prediction run on this one (the two read
+                # only the scene and the sites)
+                side = _side_stream(torch, cand.device)
+                side.wait_stream(main)
+                cp = dataclasses.replace(params, n_bands=coarse_params.n_bands, n_bins=coarse_params.n_bins,
+                                         seed=coarse_params.seed, rec_base=0, parts=0)
+                with torch.cuda.stream(side):
+                    rc = compute_records(scene, pts, cp, full=False)["radius"]
+                pts.record_stream(side)
             feat = coarse_features(scene, pts, coarse_params, bf16=True)     # read by TMA in the forward pass
             logr = mlp.predict(feat)
             offset = 0.2 * math.log(params.eps / (eps_train or params.eps))
-            rc = None
-            if fallback:
-                # the coarse ray set's own record at the placement's tolerance
-                cp = dataclasses.replace(params, n_bands=coarse_params.n_bands, n_bins=coarse_params.n_bins,
-                                         seed=coarse_params.seed, rec_base=0, parts=0)
-                rc = compute_records(scene, pts, cp, full=False)["radius"]
+            if rc is not None:
+                main.wait_stream(side)
+                rc.record_stream(main)
             logr, n_fallback = mlp_fallback(logr, offset, rc, logr_fallback=10.0)
             res.predicted_sites = m
             rep = torch.empty((n,), dtype=torch.int32, device=cand.device)

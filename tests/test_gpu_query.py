@@ -64,11 +64,12 @@ def test_synthetic_table_parity(vrc, order):
 
 
 def test_long_cell_lists(vrc):
-    """Cell lists of every length class of the grid's list sort: up to 64 entries (a warp,
-    in registers), up to 512 (a warp's shared buffer), up to 4,096 (a block's) and beyond
-    (one thread).  6,000 records of radius 0.35-0.45 around the centre give cells that hold
-    thousands of records; the answers match the oracle and are the same bits when the grid
-    is built twice (each list in record order)."""
+    """Cell lists of every length class of the grid's list sort, on a coarse grid (a block
+    per cell) and on a fine one (a warp per cell: up to 64 entries in registers, up to 512 in
+    a warp's shared buffer, longer lists a block each, beyond 4,096 one thread).  Records of
+    radius 0.35-0.45 clustered at the centre give cells that hold thousands of records; the
+    answers match the oracle and are the same bits when the grid is built twice (each list
+    in record order)."""
     rng = np.random.default_rng(41)
     n = 6000
     tab = synthetic_table(n, seed=42, r_lo=0.35, r_hi=0.45)
@@ -77,12 +78,18 @@ def test_long_cell_lists(vrc):
     small = synthetic_table(400, seed=43, r_lo=0.01, r_hi=0.03)
     tab = {k: np.concatenate([tab[k], small[k]]) for k in tab}
     q = rng.uniform(0.0, 1.0, size=(4000, 3)).astype(np.float32)
-    rgb, cnt, grid = gpu_query(vrc, tab, q, 1)
-    rgb2, cnt2, _ = gpu_query(vrc, tab, q, 1)
-    assert np.array_equal(rgb, rgb2) and np.array_equal(cnt, cnt2)
-    ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=1)
-    check_query(rgb, cnt, ref, rc, near)
-    assert cnt.max() > 4096 and (cnt < 32).any()
+    for fine in (False, True):
+        if fine:
+            # most records small (median radius 0.02: a 64^3 grid, the warp-per-cell sort),
+            # the big clustered ones still there
+            tiny = synthetic_table(8000, seed=44, r_lo=0.01, r_hi=0.03)
+            tab = {k: np.concatenate([tab[k], tiny[k]]) for k in tab}
+        rgb, cnt, grid = gpu_query(vrc, tab, q, 1)
+        rgb2, cnt2, _ = gpu_query(vrc, tab, q, 1)
+        assert np.array_equal(rgb, rgb2) and np.array_equal(cnt, cnt2)
+        ref, rc, near = O.query(tab["pos"], tab["radius"], tab["L"], tab["grad"], tab["hess"], q, order=1)
+        check_query(rgb, cnt, ref, rc, near)
+        assert cnt.max() > 4096 and (cnt < 32).any()
 
 
 @pytest.mark.parametrize("order", [1, 2])
