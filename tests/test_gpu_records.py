@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests.gpu_helpers import compare_radius, compare_records, to_np
+from tests.gpu_helpers import compare_radius, compare_records, oracle_replayed, to_np
 from workloads.configs import RecordParams
 
 pytestmark = pytest.mark.gpu
@@ -286,3 +286,19 @@ def test_prepass_in_batches_matches_in_kernel_tracing(vrc):
     b = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(no_prepass=1))
     for k in ("L", "grad", "hess", "radius", "status", "n_cells"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_largest_ray_set(vrc):
+    """The largest ray set the record kernel takes, 256 bands x 512 bins (131,074 rays, in
+    band chunks), on the small scene: three records against the oracle replaying the GPU's
+    decisions, at the bare tolerances; one more band is refused."""
+    w = W.config1()
+    rp = RecordParams(n_bands=256, n_bins=512)
+    pos = w.positions(3, seed=23)
+    g = run_gpu(vrc, w.scene, rp, pos, debug_hits=True)
+    ref = oracle_replayed(O, O.OracleScene(w.scene), rp, pos, g)
+    st = compare_records(g, ref)
+    compare_radius(g, ref)
+    assert st["n"] == 3 and st["worst_L"] <= 1.0 and st["worst_g"] <= 1.0 and st["worst_H"] <= 1.0
+    with pytest.raises(vrc.VrcError, match="unsupported"):
+        run_gpu(vrc, w.scene, RecordParams(n_bands=257, n_bins=512), pos)
