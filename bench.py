@@ -920,13 +920,13 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
             equal[k] = {"mean_rel_err": e, "outside_plain_range": [plain[0][0], plain[-1][0]]}
     sp = {k: v["speedup"] for k, v in equal.items() if "speedup" in v}
     best = max(sp, key=sp.get) if sp else None
-    verdict = ("no learned run falls inside the plain runs' error range" if best is None else
+    outcome = ("no learned run falls inside the plain runs' error range" if best is None else
                (f"learned faster than plain at equal error: best {best} {sp[best]:.2f}x" if sp[best] > 1.0 else
                 f"learned slower than plain at equal error: best {best} {sp[best]:.2f}x"))
     return {"workload": "learned: predictor trained on 16 mid-style scenes (1,048,576 records), placement on a "
                         "held-out scene (seed 41), 60,000 candidates, records 32x64, coarse features 8x16",
             "training": dict(fit, seconds=train_s, steps=steps), "runs": res, "equal_error": equal,
-            "summary": verdict, "speedups_at_equal_error": sp,
+            "summary": outcome, "speedups_at_equal_error": sp,
             "reference_noise_floor": {"mean_rel_err": float(rel_err(ref2).mean()),
                                       "rel_rmse": float(np.sqrt(np.mean((ref2 - ref) ** 2)) / np.mean(np.abs(ref)))}}
 

@@ -55,7 +55,7 @@ def test_predicts_held_out_radii(vrc, trained):
 
 
 def test_learned_placement_needs_fewer_records_at_equal_error(vrc, trained):
-    """Coverage is judged by the full records' true radii in both cases, so both placements
+    """Coverage is decided by the full records' true radii in both cases, so both placements
     honour the error tolerance; the predictor's levels alone (no coarse-record fallback) put
     the coarse-wave sites where the predicted radius is large (cell up to 1.5 x radius) and
     need fewer records."""
