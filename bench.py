@@ -807,8 +807,10 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
     and split 80/10/10 (train / validation / test; the held-out errors are reported).
     Placement runs on a held-out scene (seed 41): 60,000 candidate points covered by plain
     waves, learned waves and learned one-shot placement (every predicted level's sites in
-    one batched launch, then plain repair waves), with predictions on a 2^5, 2^4 or 2^3 grid
-    of cells (the _p4 and _p3 runs), each at 1, 1/10, 1/100 and 1/1000 of the
+    one batched launch, then plain repair waves) and learned batched waves (each wave places
+    every level's sites in one pass and one launch; uncovered candidates move one level
+    finer), with predictions on a 2^5, 2^4 or 2^3 grid of cells (the _p4 and _p3 runs), each
+    at 1, 1/10, 1/100 and 1/1000 of the
     workload's tolerance, with the predictor's radius carried to each tolerance and checked
     against the coarse record (vrc_mlp_fallback).  Error: per-point relative luminance
     error at 619 held-out candidates against a 64x128-ray record there (mean, median, 90th
@@ -875,6 +877,10 @@ def learned_comparison(n_scenes: int = 16, per_scene: int = 65536, steps: int = 
                                              predict_level=4, one_shot=True)),
                 ("learned_p3", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
                                     predict_level=3)),
+                ("learned_batched_p4", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
+                                            predict_level=4, batched=True)),
+                ("learned_batched_p3", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
+                                            predict_level=3, batched=True)),
                 ("learned_one_shot_p3", dict(mlp=mlp, coarse_params=coarse, cell_over_radius=1.5, eps_train=eps0,
                                              predict_level=3, one_shot=True)))
     res = {}

@@ -372,6 +372,21 @@ int vrc_select_sites(const float* d_pts, const int32_t* d_level, int32_t n, int3
                      int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts, int32_t* h_count,
                      int32_t* h_pool, void* stream);
 
+/* Placement wave over several levels at once (learned placement, not in the paper): every
+ * candidate with lmin <= d_level[i] <= lmax competes in its cell of the 2^d_level[i] grid,
+ * and the candidate with the smallest index in each (level, cell) is picked, so that one
+ * wave places the sites of every level.  Outputs as vrc_select_sites (*h_count sites, in
+ * ascending candidate order; *h_pool, when non-NULL, the candidates left in the pool at any
+ * level); synchronous.  lmax <= 7; d_scratch must hold (8^(lmax+1) - 8^lmin)/7 + 2 n +
+ * n/1024 + 3 ints. */
+int vrc_select_sites_levels(const float* d_pts, const int32_t* d_level, int32_t n, int32_t lmin, int32_t lmax,
+                            int32_t* d_scratch, int64_t scratch_ints, int32_t* d_site_idx, float* d_site_pts,
+                            int32_t* h_count, int32_t* h_pool, void* stream);
+
+/* d_level[i] = min(d_level[i] + 1, lmax) for the candidates still in the pool (d_level[i] >=
+ * 0): after a wave, the uncovered candidates compete on the next finer grid.  Asynchronous. */
+int vrc_bump_levels(int32_t* d_level, int32_t n, int32_t lmax, void* stream);
+
 /* Learned levels predicted once per cell: after vrc_select_sites at cell_level (which left
  * each cell's representative -- smallest candidate index -- in the first 8^cell_level
  * ints of d_scratch), d_site_logr[j] is the predicted log radius of site j (index

@@ -101,6 +101,8 @@ def load_library(path: Optional[str] = None):
     L.vrc_render.argtypes = [P, P, P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_composite.argtypes = [P, P, I32, I32, I32, I32, I32, P, P, P]
     L.vrc_select_sites.argtypes = [P, P, I32, I32, P, C.c_int64, P, P, P, P, P]
+    L.vrc_select_sites_levels.argtypes = [P, P, I32, I32, I32, P, C.c_int64, P, P, P, P, P]
+    L.vrc_bump_levels.argtypes = [P, I32, I32, P]
     L.vrc_update_coverage.argtypes = [P, I32, P, P]
     L.vrc_init_levels.argtypes = [P, I32, I32, P, P]
     L.vrc_march_pixels.argtypes = [P, P, P, I32, I32, P, P, P]
@@ -692,6 +694,19 @@ def select_sites(pts, level, wave_level: int, scratch, site_idx, site_pts, strea
                                            C.byref(pool) if with_pool else None, _stream_ptr(stream)),
            "vrc_select_sites")
     return (int(cnt.value), int(pool.value)) if with_pool else int(cnt.value)
+
+
+def select_sites_levels(pts, level, lmin: int, lmax: int, scratch, site_idx, site_pts, stream=None):
+    """vrc_select_sites_levels: (sites, candidates left in the pool)."""
+    cnt, pool = C.c_int32(0), C.c_int32(0)
+    _check(load_library().vrc_select_sites_levels(_ptr(pts), _ptr(level), pts.shape[0], lmin, lmax, _ptr(scratch),
+                                                  scratch.numel(), _ptr(site_idx), _ptr(site_pts), C.byref(cnt),
+                                                  C.byref(pool), _stream_ptr(stream)), "vrc_select_sites_levels")
+    return int(cnt.value), int(pool.value)
+
+
+def bump_levels(level, lmax: int, stream=None):
+    _check(load_library().vrc_bump_levels(_ptr(level), level.shape[0], lmax, _stream_ptr(stream)), "vrc_bump_levels")
 
 
 def levels_by_cell(pts, cell_level: int, scratch, site_idx, site_logr, n_sites: int, cell_over_radius: float,

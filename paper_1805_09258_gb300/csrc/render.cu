@@ -311,6 +311,41 @@ __global__ void k_cell_levels(const float* pts, int n, int G, const int* cell_mi
     if (rep >= 0 && rep < n) level[i] = rep_level[rep];
 }
 
+// Sites of every level at once: a candidate of level l in [lmin, lmax] claims its cell of
+// the 2^l grid; the cells of all levels share one array, level l's at offset
+// (8^l - 8^lmin) / 7.
+__device__ __forceinline__ long long ml_cell(const float* pts, int i, int l, int lmin) {
+    const int G = 1 << l;
+    const long long off = ((1ll << (3 * l)) - (1ll << (3 * lmin))) / 7;
+    int ix = min(G - 1, max(0, (int)floorf(pts[3 * i] * G)));
+    int iy = min(G - 1, max(0, (int)floorf(pts[3 * i + 1] * G)));
+    int iz = min(G - 1, max(0, (int)floorf(pts[3 * i + 2] * G)));
+    return off + ((long long)ix * G + iy) * G + iz;
+}
+
+__global__ void k_site_claim_ml(const float* pts, const int* level, int n, int lmin, int lmax, int* cell_min,
+                                int* pool) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int l = i < n ? level[i] : -1;
+    const unsigned in_pool = __ballot_sync(0xffffffffu, l >= 0);
+    if ((threadIdx.x & 31) == 0 && in_pool) atomicAdd(pool, __popc(in_pool));
+    if (l < lmin || l > lmax) return;
+    atomicMin(&cell_min[ml_cell(pts, i, l, lmin)], i);
+}
+
+__global__ void k_site_flag_ml(const float* pts, const int* level, int n, int lmin, int lmax, const int* cell_min,
+                               int* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int l = level[i];
+    flag[i] = (l >= lmin && l <= lmax && cell_min[ml_cell(pts, i, l, lmin)] == i) ? 1 : 0;
+}
+
+__global__ void k_bump_levels(int* level, int n, int lmax) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && level[i] >= 0) level[i] = min(level[i] + 1, lmax);
+}
+
 __global__ void k_retire_level(int* level, int n, int lv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && level[i] == lv) level[i] = -1;
@@ -438,6 +473,46 @@ extern "C" int vrc_select_sites(const float* d_pts, const int32_t* d_level, int3
     *h_count = both[0];
     if (h_pool) *h_pool = both[1];
     return VRC_OK;
+}
+
+extern "C" int vrc_select_sites_levels(const float* d_pts, const int32_t* d_level, int32_t n, int32_t lmin,
+                                       int32_t lmax, int32_t* d_scratch, int64_t scratch_ints, int32_t* d_site_idx,
+                                       float* d_site_pts, int32_t* h_count, int32_t* h_pool, void* stream) {
+    if (!d_pts || !d_level || n < 0 || lmin < 0 || lmax < lmin || lmax > 7 || !d_scratch || !d_site_idx ||
+        !d_site_pts || !h_count)
+        return VRC_ERR_INVALID;
+    *h_count = 0;
+    if (h_pool) *h_pool = 0;
+    if (n == 0) return VRC_OK;
+    const long long cells = ((1ll << (3 * (lmax + 1))) - (1ll << (3 * lmin))) / 7;
+    const int nblk = (n + 1023) / 1024;
+    if (scratch_ints < cells + 2LL * n + nblk + 2) return VRC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* cell_min = d_scratch;
+    int* flag = cell_min + cells;
+    int* pos = flag + n;
+    int* sums = pos + n;                  // [nblk] block sums, then the site count and the pool size
+    VRC_CUDA_CHECK(cudaMemsetAsync(cell_min, 0x7f, sizeof(int) * cells, st));
+    VRC_CUDA_CHECK(cudaMemsetAsync(sums + nblk + 1, 0, sizeof(int), st));
+    int tb = 256, nb = (n + tb - 1) / tb;
+    k_site_claim_ml<<<nb, tb, 0, st>>>(d_pts, d_level, n, lmin, lmax, cell_min, sums + nblk + 1);
+    k_site_flag_ml<<<nb, tb, 0, st>>>(d_pts, d_level, n, lmin, lmax, cell_min, flag);
+    k_flag_scan<<<nblk, 1024, 0, st>>>(flag, n, pos, sums);
+    k_flag_tops<<<1, 32, 0, st>>>(sums, nblk, sums + nblk);
+    k_gather_sites<<<nb, tb, 0, st>>>(d_pts, flag, pos, sums, n, d_site_idx, d_site_pts);
+    int32_t both[2] = {0, 0};
+    VRC_CUDA_CHECK(cudaMemcpyAsync(both, sums + nblk, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    VRC_CUDA_CHECK(cudaStreamSynchronize(st));
+    *h_count = both[0];
+    if (h_pool) *h_pool = both[1];
+    return VRC_OK;
+}
+
+extern "C" int vrc_bump_levels(int32_t* d_level, int32_t n, int32_t lmax, void* stream) {
+    if (n < 0 || (n > 0 && !d_level)) return VRC_ERR_INVALID;
+    if (n == 0) return VRC_OK;
+    k_bump_levels<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_level, n, lmax);
+    return cudaGetLastError() == cudaSuccess ? VRC_OK : VRC_ERR_CUDA;
 }
 
 extern "C" int vrc_update_coverage(const int32_t* d_count, int32_t n, int32_t* d_level, void* stream) {

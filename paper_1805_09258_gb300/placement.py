@@ -19,7 +19,12 @@ to the placement's tolerance (R goes as eps^(1/5), Eq. radiusAniso3D), and it is
 where a record of the coarse ray set itself puts the error at the predicted radius within
 the tolerance (vrc_mlp_fallback); elsewhere the candidate falls back to plain placement.
 
-One-shot (batched) learned placement selects the sites of every predicted level at once
+Batched learned placement places the sites of every predicted level in each wave: one
+selection pass over all levels (vrc_select_sites_levels), one record launch, one grid
+build and one coverage query per wave; the candidates a wave leaves uncovered move one
+level finer (vrc_bump_levels) for the next wave.
+
+One-shot learned placement selects the sites of every predicted level at once
 (level by level on a copy of the pool, vrc_retire_level) and computes all their records
 in one persistent launch, with one grid build and one coverage query; the few candidates
 left uncovered then go through the plain waves at their predicted levels.
@@ -34,8 +39,9 @@ from dataclasses import dataclass, field
 import dataclasses
 import math
 
-from . import (MLP, Grid, Scene, alloc_records, coarse_features, compute_records, init_levels, levels_by_cell,
-               levels_from_radius, mlp_fallback, query_inscatter, retire_level, select_sites, update_coverage,
+from . import (MLP, Grid, Scene, alloc_records, bump_levels, coarse_features, compute_records, init_levels,
+               levels_by_cell, levels_from_radius, mlp_fallback, query_inscatter, retire_level, select_sites,
+               select_sites_levels, update_coverage,
                _torch)
 
 
@@ -65,7 +71,7 @@ class PlacementResult:
 def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, mlp: MLP = None,
           coarse_params=None, cell_over_radius: float = 1.0, capacity: int = None, valid=None,
           base: PlacementResult = None, predict_level: int = 5, aniso: bool = False, eps_train: float = None,
-          fallback: bool = True, one_shot: bool = False) -> PlacementResult:
+          fallback: bool = True, one_shot: bool = False, batched: bool = False) -> PlacementResult:
     """Place records until every candidate point `cand` [n,3] (CUDA float32) is covered.
 
     valid [n] (int32, nullable): only nonzero entries are candidates.  base: an earlier
@@ -73,7 +79,8 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
     aniso: records cover their ellipsoids (anisotropic cache points) instead of spheres.
     Learned placement (mlp given): eps_train is the tolerance the predictor was trained at
     (default params.eps); fallback applies the coarse-record check; one_shot places every
-    predicted level's sites in one batched launch before the waves.
+    predicted level's sites in one batched launch before the waves; batched runs every wave
+    over all levels at once (uncovered candidates one level finer after each).
     """
     torch = _torch()
     n = cand.shape[0]
@@ -165,13 +172,25 @@ def place(scene: Scene, params, cand, start_level: int = 2, max_level: int = 7, 
         if got:
             add_records(batch, got)
     in_pool = n
-    for lv in range(start_level, max_level + 1):
-        m, in_pool = select_sites(cand, level, lv, scratch, site_idx, site_pts, with_pool=True)
-        if in_pool == 0:
-            break                         # every candidate is covered: the finer waves are empty
-        res.waves.append((lv, m))
-        if m:
+    if batched and mlp is not None:
+        # every level's sites in one wave (one selection pass, one record launch, one grid
+        # build and coverage query); the candidates a wave leaves uncovered move one level
+        # finer for the next; those past max_level go to the fine fill below
+        while True:
+            m, in_pool = select_sites_levels(cand, level, start_level, max_level, scratch, site_idx, site_pts)
+            if in_pool == 0 or m == 0:
+                break
+            res.waves.append(("levels", m))
             add_records(site_pts, m)
+            bump_levels(level, fine)
+    else:
+        for lv in range(start_level, max_level + 1):
+            m, in_pool = select_sites(cand, level, lv, scratch, site_idx, site_pts, with_pool=True)
+            if in_pool == 0:
+                break                         # every candidate is covered: the finer waves are empty
+            res.waves.append((lv, m))
+            if m:
+                add_records(site_pts, m)
     # candidates still uncovered get sites on the finest grid until none is left (each
     # wave covers at least its own sites, so this ends)
     left = 0 if in_pool == 0 else select_sites(cand, level, fine, scratch, site_idx, site_pts)

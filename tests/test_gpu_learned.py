@@ -128,3 +128,49 @@ def test_fallback_rule_and_one_shot_placement(vrc, trained):
         want = int(np.sum(~(np.exp(pred) <= rc * (1 + 1e-6))))
         assert m == r.predicted_sites
         assert abs(r.fallback_sites - want) <= max(2, m // 1000), (r.fallback_sites, want, m)
+
+
+def test_multi_level_sites_and_batched_placement(vrc, trained):
+    """One selection pass over several levels picks, in every (level, cell) of the candidates'
+    own levels, the smallest candidate index (checked against numpy); the pool count and
+    the level bump do what they say; batched learned placement (each wave over all levels,
+    uncovered candidates one level finer after it) covers every candidate."""
+    from paper_1805_09258_gb300 import placement
+    rng = np.random.default_rng(9)
+    n = 5000
+    pts_np = rng.uniform(0.0, 1.0, size=(n, 3)).astype(np.float32)
+    lev_np = rng.integers(0, 9, size=n).astype(np.int32) - 1            # -1 .. 7
+    lev_np[lev_np == 0] = -1
+    lev_np[lev_np == 1] = 2
+    pts = torch.from_numpy(pts_np).cuda()
+    level = torch.from_numpy(lev_np).cuda()
+    scratch = torch.empty(((8 ** 8 - 8 ** 2) // 7 + 2 * n + n // 1024 + 3,), dtype=torch.int32, device="cuda")
+    site_idx = torch.empty((n,), dtype=torch.int32, device="cuda")
+    site_pts = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    m, pool = vrc.select_sites_levels(pts, level, 2, 7, scratch, site_idx, site_pts)
+    best = {}
+    for i in range(n):
+        l = int(lev_np[i])
+        if 2 <= l <= 7:
+            g = 1 << l
+            c = tuple(np.minimum(np.floor(pts_np[i] * np.float32(g)).astype(np.int64), g - 1))
+            best.setdefault((l, c), i)
+    want = sorted(best.values())
+    got = site_idx[:m].cpu().numpy()
+    assert m == len(want) and np.array_equal(got, want)
+    assert np.array_equal(site_pts[:m].cpu().numpy(), pts_np[want])
+    assert pool == int((lev_np >= 0).sum())
+    vrc.bump_levels(level, 8)
+    assert np.array_equal(level.cpu().numpy(), np.where(lev_np >= 0, np.minimum(lev_np + 1, 8), -1))
+
+    mlp = trained[0]
+    w = W.config4(scene_seed=41)
+    s = vrc.Scene.from_workload(w.scene)
+    cand = torch.from_numpy(w.positions(60000, seed=441)).cuda()
+    for eps in (w.params.eps, w.params.eps / 10):
+        rp = W.configs.replace(w.params, eps=eps)
+        r = placement.place(s, rp, cand, mlp=mlp, coarse_params=COARSE, cell_over_radius=1.5,
+                            eps_train=w.params.eps, predict_level=3, batched=True)
+        _, cnt = vrc.query_inscatter(r.grid, cand)
+        assert int((cnt == 0).sum()) == 0
+        assert any(wv[0] == "levels" for wv in r.waves)
