@@ -165,11 +165,12 @@ typedef struct {
     int32_t dbg_shells;
 } vrc_records_view;
 
-/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default: for
- * small ray sets (whole set within 36 KB) and at least 6 records per SM, 128 threads with the
- * whole ray set (six blocks per SM); else 384 threads with the whole ray set in shared memory
- * when that fits two blocks per SM (up to 110 KB); else 256 threads with as many bands per
- * chunk as fit 72 KB (three blocks). */
+/* Launch shape of the record kernel (see vrc_autotune_records). 0 = library default: for at
+ * most one record per SM, 512 threads with the whole ray set (up to 200 KB); for small ray
+ * sets (whole set within 36 KB) and at least 6 records per SM, 128 threads with the whole ray
+ * set (six blocks per SM); else 384 threads with the whole ray set in shared memory when that
+ * fits two blocks per SM (up to 110 KB); else 256 threads with as many bands per chunk as fit
+ * 72 KB (three blocks). */
 typedef struct {
     int32_t threads;        /* threads per block: 128, 256, 384, 512 */
     int32_t chunk_bands;    /* bands of the ray set kept in shared memory at once */

@@ -1358,15 +1358,23 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
     if (p->parts < 0 || p->parts > 2) return VRC_ERR_INVALID;
     if (nb > 256 || ns > 512) return VRC_ERR_UNSUPPORTED;
     if (p->lo_grad && s->dev.n_lights != 1) return VRC_ERR_UNSUPPORTED;   // one light's phase per vertex
-    if (p->lo_grad && s->tuning.threads != 0 && s->tuning.threads != 256 && s->tuning.threads != 384)
-        return VRC_ERR_UNSUPPORTED;                     // compiled for the two default block shapes
+    if (p->lo_grad && s->tuning.threads != 0 && s->tuning.threads != 256 && s->tuning.threads != 384 &&
+        s->tuning.threads != 512)
+        return VRC_ERR_UNSUPPORTED;                     // compiled for the default block shapes
     if ((out->hit_prim != nullptr) != (out->hit_t != nullptr)) return VRC_ERR_INVALID;
     if (out->hit_prim && out->dbg_stride < nb * ns + 2) return VRC_ERR_INVALID;
     if (out->dbg_lit && (!out->hit_prim || out->dbg_shells < 1)) return VRC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     int nt = s->tuning.threads ? s->tuning.threads : 256;
     int cb = s->tuning.chunk_bands;
-    if (!s->tuning.threads && cb <= 0 && !p->lo_grad && n >= 6 * s->sm_count &&
+    if (!s->tuning.threads && cb <= 0 && n <= s->sm_count && record_smem_bytes((nb + 1) * ns + 2, 512) <= 200 * 1024) {
+        // at most one record per SM (placement's small waves): one block of 512 threads per
+        // record with the whole ray set, 16 warps on its shells instead of 12 (measured, 32 x
+        // 64 rays: 4 records 0.217 -> 0.182 ms, 150 records 0.286 -> 0.243 ms; at 304 and
+        // more records two blocks of 384 per SM stay faster; 768 threads: slower than 512)
+        nt = 512;
+        cb = nb;
+    } else if (!s->tuning.threads && cb <= 0 && !p->lo_grad && n >= 6 * s->sm_count &&
         record_smem_bytes((nb + 1) * ns + 2, 128) <= 36 * 1024) {
         // small ray sets (up to about 16 x 32) and enough records to fill six blocks per SM:
         // blocks of 128 threads with the whole ray set, so that a record's few vertex and
@@ -1437,8 +1445,10 @@ extern "C" int vrc_compute_records(vrc_scene* s, const float* d_pos, int32_t n, 
         k_lpt_scatter<<<nbk, 256, 0, st>>>(d_n_bands, n, hist, s->d_order);
         a.order = s->d_order;
     }
-    if (a.lo_grad)   // compiled for the two default block shapes only
-        return nt == 384 ? launch_records<384, true>(s, a, smem, st) : launch_records<256, true>(s, a, smem, st);
+    if (a.lo_grad)   // compiled for the default block shapes only (not the 128-thread one)
+        return nt == 384 ? launch_records<384, true>(s, a, smem, st)
+                         : (nt == 512 ? launch_records<512, true>(s, a, smem, st)
+                                      : launch_records<256, true>(s, a, smem, st));
     switch (nt) {
         case 128: return launch_records<128>(s, a, smem, st);
         case 384: return launch_records<384>(s, a, smem, st);
