@@ -60,7 +60,7 @@ def cpu_model() -> str:
 
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled during the timed region: through NVML
-    (the driver's libnvidia-ml, read-only queries) every 10 ms, so that a timed region of a few
+    (NVIDIA's libnvidia-ml from the GPU driver, read-only queries) every 10 ms, so that a timed region of a few
     tens of milliseconds still gets several samples; nvidia-smi every 200 ms if NVML cannot be
     loaded."""
 

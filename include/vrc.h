@@ -467,7 +467,7 @@ int vrc_mlp_predict(const vrc_mlp* mlp, const float* d_feat, int32_t n, float* d
  * 128-row tile is copied from HBM into the tensor cores' operand layout by the tensor
  * memory accelerator (tiled bulk copies, 128-byte swizzle), half the bytes of the FP32
  * path; the result equals vrc_mlp_predict on the same features rounded to BF16.
- * VRC_ERR_UNSUPPORTED when the driver offers no tensor-map encoder.  Asynchronous. */
+ * VRC_ERR_UNSUPPORTED when the CUDA driver offers no tensor-map encoder.  Asynchronous. */
 int vrc_mlp_predict_bf16(const vrc_mlp* mlp, const void* d_feat, int32_t n, float* d_logr, void* stream);
 int vrc_mlp_gradient(vrc_mlp* mlp, const float* d_feat, const float* d_target, int32_t n, float* d_grad,
                      float* d_pred, void* stream);
