@@ -60,9 +60,9 @@ def cpu_model() -> str:
 
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled during the timed region: through NVML
-    (NVIDIA's libnvidia-ml from the GPU driver, read-only queries) every 10 ms, so that a timed region of a few
-    tens of milliseconds still gets several samples; nvidia-smi every 200 ms if NVML cannot be
-    loaded."""
+    (NVIDIA's libnvidia-ml from the GPU driver, read-only queries) every 10 ms, so that a timed
+    region of a few tens of milliseconds still gets several samples; nvidia-smi every 200 ms if
+    NVML cannot be loaded."""
 
     # NVML clock-event reason bits (nvml.h)
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
