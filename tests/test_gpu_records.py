@@ -302,3 +302,21 @@ def test_largest_ray_set(vrc):
     assert st["n"] == 3 and st["worst_L"] <= 1.0 and st["worst_g"] <= 1.0 and st["worst_H"] <= 1.0
     with pytest.raises(vrc.VrcError, match="unsupported"):
         run_gpu(vrc, w.scene, RecordParams(n_bands=257, n_bins=512), pos)
+
+
+def test_many_small_ray_sets_in_128_thread_blocks(vrc):
+    """1,000 records of 16 x 32 rays (enough to fill six 128-thread blocks per SM, the
+    launch shape such sets get by default) on the small scene: a sample of 64 against the
+    oracle replaying the GPU's decisions, at the bare tolerances, and every record equal to
+    the 384-thread launch up to the order of the sums."""
+    w = W.config1()
+    pos = w.positions(1000, seed=29)
+    g = run_gpu(vrc, w.scene, w.params, pos, debug_hits=True)
+    sel = np.arange(3, 1000, 16)
+    ref = oracle_replayed(O, O.OracleScene(w.scene), w.params, pos[sel], g, rec_ids=sel, idx=sel)
+    st = compare_records(g, ref, idx=sel)
+    assert st["worst_L"] <= 1.0 and st["worst_g"] <= 1.0 and st["worst_H"] <= 1.0
+    g384 = run_gpu(vrc, w.scene, w.params, pos, tuning=dict(threads=384))
+    for k in ("L", "grad", "hess"):
+        scale = np.abs(g384[k]).max(axis=1, keepdims=True) + 1e-30
+        assert np.all(np.abs(g[k] - g384[k]) <= 1e-4 * scale), k
